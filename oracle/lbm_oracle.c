@@ -51,9 +51,11 @@ struct orc_sim {
   long long t;
   /* state */
   double *f, *g, *fn, *gn;
-  /* per-step work fields, [ny][nx] unless noted */
+  /* per-step work fields.  Moments n, phi, mx, my: [ny][nx].  The fields
+   * of the collision (mu, gradient, u, C, F_y) live on the extended rows
+   * -1..ny ([ny+2][nx]); phih on rows -2..ny+1 ([ny+4][nx]). */
   double *n, *phi, *mx, *my, *mu, *dpx, *dpy, *ux, *uy, *C, *Fy;
-  double *phih;          /* [ny+2][nx]: phi with ghost values, rows -1..ny */
+  double *phih;          /* phi with ghost values on solid points */
   double *fs;            /* [9][ny+2][nx]: post-collision f, rows -1..ny */
   double *P;             /* [5][ny+2][nx]: moving part of g, rows -1..ny */
   double *S;             /* [5][ny][nx]: staying part; S[0] = g0 + Omega_0 */
@@ -228,43 +230,34 @@ static double ghost_value(const orc_sim* s, const double* phi, int x, int y) {
   return cnt ? sum / cnt : 0.0;
 }
 
-/* Fill phih (rows -1..ny) with phi on fluid points and ghost values on
- * solid ones. */
+/* The axial ends extend the lattice: outside rows take the mapped row's
+ * phi and geometry (replicated edge rows for the zero-gradient ends, wrapped
+ * rows for periodic ends) and every rule is then applied on the extended
+ * lattice; outside a closed domain lie non-wetting solid rows.
+ * fill_phih: phi on fluid points and ghost values on solid points, for the
+ * extended rows -2..ny+1. */
 static void fill_phih(orc_sim* s, const double* phi) {
   int nx = s->nx, ny = s->ny;
-  for (int y = 0; y < ny; y++)
-    for (int x = 0; x < nx; x++) {
-      size_t c = (size_t)y * nx + x;
-      s->phih[(size_t)(y + 1) * nx + x] = s->kind[c] == 0 ? phi[c] : ghost_value(s, phi, x, y);
-    }
-  for (int e = 0; e < 2; e++) {
-    int y = e == 0 ? -1 : ny;
-    int ym;
-    for (int x = 0; x < nx; x++) {
-      double v;
-      if (map_y(s, y, &ym))
-        v = s->phih[(size_t)(ym + 1) * nx + x];
-      else
-        v = ghost_value(s, phi, x, y);
-      s->phih[(size_t)(y + 1) * nx + x] = v;
-    }
-  }
+  for (int y = -2; y < ny + 2; y++)
+    for (int x = 0; x < nx; x++)
+      s->phih[(size_t)(y + 2) * nx + x] =
+          kind_at(s, x, y) == 0 ? phi_fluid_at(s, phi, x, y) : ghost_value(s, phi, x, y);
 }
 
 static double phih_at(const orc_sim* s, int x, int y) {
-  return s->phih[(size_t)(y + 1) * s->nx + wrap(x, s->nx)];
+  return s->phih[(size_t)(y + 2) * s->nx + wrap(x, s->nx)];
 }
 
 /* Chemical potential and gradient on fluid points from the isotropic D2Q9
  * stencils: lap = 6 sum_i w_i (phi(x+c_i) - phi(x)), grad = 3 sum_i w_i c_i
  * phi(x+c_i); mu = 4 A phi (phi^2 - phi*^2) - kappa lap. */
-static void chem_potential(orc_sim* s, const double* phi) {
+static void chem_potential(orc_sim* s) {
   int nx = s->nx, ny = s->ny;
-  for (int y = 0; y < ny; y++)
+  for (int y = -1; y <= ny; y++)
     for (int x = 0; x < nx; x++) {
-      size_t c = (size_t)y * nx + x;
-      if (s->kind[c] != 0) continue;
-      double p0 = phi[c];
+      size_t c = (size_t)(y + 1) * nx + x;
+      if (kind_at(s, x, y) != 0) continue;
+      double p0 = phih_at(s, x, y);
       double lap = 0.0, gx = 0.0, gy = 0.0;
       for (int i = 1; i < 9; i++) {
         double pn = phih_at(s, x + EX[i], y + EY[i]);
@@ -291,7 +284,7 @@ orc_sim* orc_create(const orc_params* p) {
   s->nx = p->nx;
   s->ny = p->ny;
   int nx = s->nx, ny = s->ny;
-  size_t N = (size_t)nx * ny, NM = (size_t)nx * (ny + 2);
+  size_t N = (size_t)nx * ny, NM = (size_t)nx * (ny + 2), NH = (size_t)nx * (ny + 4);
   /* derived constants (free energy, relaxation, wetting) */
   s->phis = 0.5 * (p->rho_ink - p->rho_air);
   s->n0 = 0.5 * (p->rho_ink + p->rho_air);
@@ -311,9 +304,11 @@ orc_sim* orc_create(const orc_params* p) {
   s->g = calloc(5 * N, sizeof(double));
   s->fn = calloc(9 * N, sizeof(double));
   s->gn = calloc(5 * N, sizeof(double));
-  double** w[] = {&s->n, &s->phi, &s->mx, &s->my, &s->mu, &s->dpx, &s->dpy, &s->ux, &s->uy, &s->C, &s->Fy};
+  double** w[] = {&s->n, &s->phi, &s->mx, &s->my};
   for (size_t k = 0; k < sizeof(w) / sizeof(w[0]); k++) *w[k] = calloc(N, sizeof(double));
-  s->phih = calloc(NM, sizeof(double));
+  double** we[] = {&s->mu, &s->dpx, &s->dpy, &s->ux, &s->uy, &s->C, &s->Fy};
+  for (size_t k = 0; k < sizeof(we) / sizeof(we[0]); k++) *we[k] = calloc(NM, sizeof(double));
+  s->phih = calloc(NH, sizeof(double));
   s->fs = calloc(9 * NM, sizeof(double));
   s->P = calloc(5 * NM, sizeof(double));
   s->S = calloc(5 * N, sizeof(double));
@@ -363,12 +358,13 @@ orc_sim* orc_create(const orc_params* p) {
     }
   /* initial mu from the initial phi (with wetting ghosts); n = n0, u = 0 */
   fill_phih(s, s->phi);
-  chem_potential(s, s->phi);
+  chem_potential(s);
   for (size_t c = 0; c < N; c++) {
     double fe[9], ge[5];
     if (s->kind[c] != 0) continue;
-    orc_feq(s->n0, s->phi[c], s->mu[c], 0.0, 0.0, fe);
-    orc_geq(s->phi[c], s->mu[c], 0.0, 0.0, s->gamma, s->q, ge);
+    double mu = s->mu[c + (size_t)nx];
+    orc_feq(s->n0, s->phi[c], mu, 0.0, 0.0, fe);
+    orc_geq(s->phi[c], mu, 0.0, 0.0, s->gamma, s->q, ge);
     for (int i = 0; i < 9; i++) s->f[i * N + c] = fe[i];
     for (int i = 0; i < 5; i++) s->g[i * N + c] = ge[i];
   }
@@ -434,66 +430,64 @@ static void moments(orc_sim* s) {
 }
 
 /* Pass 4 (Eq. 2, 4): total force mu grad(phi) + F_b and the half-force
- * velocity. */
+ * velocity, on the extended rows. */
 static void velocity(orc_sim* s, long long t) {
   int nx = s->nx, ny = s->ny;
   double Fd = drive_at(&s->p, t);
-  for (int y = 0; y < ny; y++)
+  for (int y = -1; y <= ny; y++) {
+    int ym;
+    if (!map_y(s, y, &ym)) continue;
     for (int x = 0; x < nx; x++) {
-      size_t c = (size_t)y * nx + x;
+      size_t c = (size_t)ym * nx + x, e = (size_t)(y + 1) * nx + x;
       if (s->kind[c] != 0) continue;
       double C = ink_fraction(s, s->phi[c]);
-      double Fb = in_drive_region(s, x, y) ? Fd * C : 0.0;
-      double Fx = s->mu[c] * s->dpx[c];
-      double Fy = s->mu[c] * s->dpy[c] + Fb;
-      s->C[c] = C;
-      s->Fy[c] = Fy;
-      s->ux[c] = (s->mx[c] + 0.5 * Fx) / s->n[c];
-      s->uy[c] = (s->my[c] + 0.5 * Fy) / s->n[c];
+      double Fb = in_drive_region(s, x, ym) ? Fd * C : 0.0;
+      double Fx = s->mu[e] * s->dpx[e];
+      double Fy = s->mu[e] * s->dpy[e] + Fb;
+      s->C[e] = C;
+      s->Fy[e] = Fy;
+      s->ux[e] = (s->mx[c] + 0.5 * Fx) / s->n[c];
+      s->uy[e] = (s->my[c] + 0.5 * Fy) / s->n[c];
     }
+  }
 }
 
-/* Pass 5: collision of f (Eq. 4-6) and of g (Eq. 8-10). */
+/* Pass 5: collision of f (Eq. 4-6) and of g (Eq. 8-10), on the extended
+ * rows (an outside row collides the populations of its mapped row). */
 static void collide(orc_sim* s) {
   int nx = s->nx, ny = s->ny;
   size_t N = (size_t)nx * ny, NM = (size_t)nx * (ny + 2);
   const orc_params* p = &s->p;
-  for (int y = 0; y < ny; y++)
+  for (int y = -1; y <= ny; y++) {
+    int ym;
+    if (!map_y(s, y, &ym)) continue;
     for (int x = 0; x < nx; x++) {
-      size_t c = (size_t)y * nx + x, cm = (size_t)(y + 1) * nx + x;
+      size_t c = (size_t)ym * nx + x, e = (size_t)(y + 1) * nx + x;
       if (s->kind[c] != 0) continue;
-      double C = s->C[c];
+      double C = s->C[e];
       double nu = p->nu_air + C * (p->nu_ink - p->nu_air);
       double tau = 0.5 + 3.0 * nu;
-      double Fx = s->mu[c] * s->dpx[c];
-      double Fy = s->Fy[c];
+      double Fx = s->mu[e] * s->dpx[e];
+      double Fy = s->Fy[e];
       double fe[9], Fi[9], ge[5];
-      orc_feq(s->n[c], s->phi[c], s->mu[c], s->ux[c], s->uy[c], fe);
-      orc_force_term(tau, s->ux[c], s->uy[c], Fx, Fy, Fi);
+      orc_feq(s->n[c], s->phi[c], s->mu[e], s->ux[e], s->uy[e], fe);
+      orc_force_term(tau, s->ux[e], s->uy[e], Fx, Fy, Fi);
       for (int i = 0; i < 9; i++) {
         double fi = s->f[i * N + c];
-        s->fs[i * NM + cm] = fi + (fe[i] - fi) / tau + Fi[i];
+        s->fs[i * NM + e] = fi + (fe[i] - fi) / tau + Fi[i];
       }
-      orc_geq(s->phi[c], s->mu[c], s->ux[c], s->uy[c], s->gamma, s->q, ge);
+      orc_geq(s->phi[c], s->mu[e], s->ux[e], s->uy[e], s->gamma, s->q, ge);
+      int inside = y >= 0 && y < ny;
       for (int i = 0; i < 5; i++) {
         double gi = s->g[i * N + c];
         double om = (ge[i] - gi) / p->tau_phi;
         if (i == 0) {
-          s->S[c] = gi + om;
+          if (inside) s->S[c] = gi + om;
         } else {
-          s->P[i * NM + cm] = s->q * gi + om;
-          s->S[i * N + c] = (1.0 - s->q) * gi;
+          s->P[i * NM + e] = s->q * gi + om;
+          if (inside) s->S[i * N + c] = (1.0 - s->q) * gi;
         }
       }
-    }
-  /* post-collision values of the rows just outside the domain */
-  for (int e = 0; e < 2; e++) {
-    int y = e == 0 ? -1 : ny, ym;
-    if (!map_y(s, y, &ym)) continue;
-    for (int x = 0; x < nx; x++) {
-      size_t dst = (size_t)(y + 1) * nx + x, src = (size_t)(ym + 1) * nx + x;
-      for (int i = 0; i < 9; i++) s->fs[i * NM + dst] = s->fs[i * NM + src];
-      for (int i = 1; i < 5; i++) s->P[i * NM + dst] = s->P[i * NM + src];
     }
   }
 }
@@ -560,9 +554,9 @@ void orc_stream_only(orc_sim* s, const double* fin, const double* gin, double* f
     int y = e == 0 ? -1 : ny, ym;
     if (!map_y(s, y, &ym)) continue;
     for (int x = 0; x < nx; x++) {
-      size_t dst = (size_t)(y + 1) * nx + x, src = (size_t)(ym + 1) * nx + x;
-      for (int i = 0; i < 9; i++) s->fs[i * NM + dst] = s->fs[i * NM + src];
-      for (int i = 1; i < 5; i++) s->P[i * NM + dst] = s->P[i * NM + src];
+      size_t dst = (size_t)(y + 1) * nx + x, src = (size_t)ym * nx + x;
+      for (int i = 0; i < 9; i++) s->fs[i * NM + dst] = fin[i * N + src];
+      for (int i = 1; i < 5; i++) s->P[i * NM + dst] = gin[i * N + src];
     }
   }
   double *f0 = s->f, *g0 = s->g;
@@ -601,14 +595,14 @@ static void diagnose(orc_sim* s, long long t) {
     for (int x = 0; x < nx; x++) {
       size_t c = (size_t)y * nx + x;
       if (s->kind[c] != 0) continue;
-      double e = s->phi[c] / s->phis, n = s->n[c];
+      double e = s->phi[c] / s->phis, n = s->n[c], uy = s->uy[c + (size_t)nx];
       e = e < 0.0 ? 0.0 : (e > 1.0 ? 1.0 : e);
       w += e;
       m += e * n;
-      pr += e * n * s->uy[c];
+      pr += e * n * uy;
       mass_n += n;
       mass_phi += s->phi[c];
-      mom_y += n * s->uy[c];
+      mom_y += n * uy;
     }
     s->wrow[y] = w;
     s->mrow[y] = m;
@@ -684,7 +678,7 @@ int orc_history(const orc_sim* s, double* out, int max_records) {
 static void step_once(orc_sim* s) {
   moments(s);
   fill_phih(s, s->phi);
-  chem_potential(s, s->phi);
+  chem_potential(s);
   velocity(s, s->t);
   if (s->p.diag_every > 0 && s->t % s->p.diag_every == 0) diagnose(s, s->t);
   collide(s);
@@ -700,14 +694,15 @@ void orc_fields(orc_sim* s, double* n, double* phi, double* mu, double* ux, doub
   size_t N = (size_t)s->nx * s->ny;
   moments(s);
   fill_phih(s, s->phi);
-  chem_potential(s, s->phi);
+  chem_potential(s);
   velocity(s, s->t);
   for (size_t c = 0; c < N; c++) {
     int fl = s->kind[c] == 0;
+    size_t e = c + (size_t)s->nx;
     if (n) n[c] = fl ? s->n[c] : 0.0;
     if (phi) phi[c] = fl ? s->phi[c] : 0.0;
-    if (mu) mu[c] = fl ? s->mu[c] : 0.0;
-    if (ux) ux[c] = fl ? s->ux[c] : 0.0;
-    if (uy) uy[c] = fl ? s->uy[c] : 0.0;
+    if (mu) mu[c] = fl ? s->mu[e] : 0.0;
+    if (ux) ux[c] = fl ? s->ux[e] : 0.0;
+    if (uy) uy[c] = fl ? s->uy[e] : 0.0;
   }
 }
