@@ -1,0 +1,296 @@
+#!/usr/bin/env python
+"""Throughput of the fused binary-fluid LBM inkjet step on GB300.
+
+Default workload: the 200 x 1600 nozzle sweep (contact angle x surface
+tension, 20 lattices, 6.4M cells, 717 MB of FP32 state -- larger than L2),
+all 20 lattices advanced together, one step = one time step of every lattice
+(fused step kernel, plus the FP64 diagnostics every 10 steps).
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS & %HBM peak, plain vs batched/FP16-store LBM; surrogate speedup at err"
+BYTES_PER_LUP = 112  # (9 + 5) FP32 populations read once and written once
+FALLBACK_HBM_GBS = 6800.0
+# DRAM bytes per step-kernel launch from an ncu capture (dram__bytes_read.sum
+# + dram__bytes_write.sum) of the workload below, valid only for the kernel
+# source whose sha256 prefix is recorded with it.
+NCU_TRAFFIC = {}
+
+
+def kernel_hash():
+    with open(os.path.join(ROOT, "paper_1702_04487_gb300", "csrc", "lbm2d_kernels.cu"), "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def workload(name, rank=0):
+    from paper_1702_04487_gb300 import workloads as W
+    if name == "cfg2":
+        ps = W.cfg2_sweep(seed=2 + rank)
+        desc = "200x1600 nozzle sweep: 5 contact angles x 4 surface tensions, 20 lattices, FP32"
+    elif name == "big":
+        ps = [W.big_nozzle()]
+        desc = "2048x8192 nozzle (200x1600 geometry scaled), 1 lattice, FP32"
+    elif name == "cfg3":
+        ps = W.cfg3_sample(seed=3 + 1000 * rank)
+        desc = "256 uneven nozzle lattices (w in [16,48], 4w x 30w), FP32"
+    else:
+        raise SystemExit("unknown workload " + name)
+    return ps, desc
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        for key in ("hbm_gbs", "hbm_GBs", "hbm"):
+            if key in d:
+                return float(d[key]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(params, seconds=12.0):
+    """The FP64 oracle, as it stands, on one lattice of the workload."""
+    from oracle import OracleSim
+    p = params[0]
+    sim = OracleSim(p)
+    cells = p["nx"] * p["ny"]
+    t0 = time.perf_counter()
+    sim.step(2)
+    per = (time.perf_counter() - t0) / 2
+    n = max(2, int(seconds / max(per, 1e-6)))
+    t0 = time.perf_counter()
+    sim.step(n)
+    dt = time.perf_counter() - t0
+    return {"value": cells * n / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": "%d steps of one %dx%d lattice (lattice 0 of the workload), FP64, "
+                      "single-threaded C" % (n, p["nx"], p["ny"])}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    params, desc = workload(args.workload)
+    from oracle import OracleSim
+    p = params[0]
+    sim = OracleSim(p)
+    cells = p["nx"] * p["ny"]
+    sim.step(args.warmup)
+    t0 = time.perf_counter()
+    sim.step(args.steps)
+    dt = time.perf_counter() - t0
+    value = cells * args.steps / dt / 1e6
+    sample = ("each step: one time step of lattice 0 (%dx%d) of the workload, FP64 oracle, "
+              "single-threaded C" % (p["nx"], p["ny"]))
+    print(json.dumps({
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "impl": "reference",
+        "config": {"workload": desc, "lattices": len(params), "cells_per_step": cells},
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def run_native(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    from paper_1702_04487_gb300 import inkjet
+
+    params, desc = workload(args.workload, rank)
+    cells = sum(p["nx"] * p["ny"] for p in params)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-resident throughput
+    h = inkjet.ij_create(params)
+    inkjet.ij_step(h, args.warmup)
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    n0 = inkjet.ij_launch_count(h)
+    inkjet.ij_kernel_timing(h, 1)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    inkjet.ij_step(h, args.steps)
+    ev1.record(stream)
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    k_ms, k_launches = inkjet.ij_kernel_timing(h, 0)
+    launches = inkjet.ij_launch_count(h) - n0
+    clk = clocks.stop()
+    obs, _ = inkjet.ij_observe(h, 0, phi=False)
+    inkjet.ij_destroy(h)
+    t = torch.tensor([ms], device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = cells * args.steps * world / (ms_max / 1e3) / 1e6
+
+    # ---- end to end through the public API, host buffers
+    import numpy as np
+    barrier()
+    t0 = time.perf_counter()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    h2 = inkjet.ij_create(params)  # host parameter blocks -> device, initialisation
+    inkjet.ij_step(h2, args.steps)
+    phis = [inkjet.ij_observe(h2, k)[1] for k in range(len(params))]  # phi + record -> host
+    e1.record(stream)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    inkjet.ij_destroy(h2)
+    te = torch.tensor([e2e_s], device="cuda")
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = cells * args.steps * world / float(te.item()) / 1e6
+    h2d = len(params) * inkjet.C.sizeof(inkjet.ij_params)
+    d2h = sum(ph.nbytes for ph in phis) + len(params) * inkjet.C.sizeof(inkjet.ij_obs)
+
+    if rank == 0:
+        peak, peak_kind = measured_peaks()
+        per_launch_ms = k_ms / max(k_launches, 1)
+        launch_cells = cells  # one launch of the step kernel advances every lattice
+        achieved = BYTES_PER_LUP * launch_cells / (per_launch_ms / 1e3) / 1e9
+        traffic = None
+        rec = NCU_TRAFFIC.get(args.workload)
+        if rec and rec.get("kernel_sha") == kernel_hash():
+            traffic = rec["bytes_per_launch"]
+        line = {
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": desc, "lattices": len(params), "cells_per_step": cells,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (%.0f MB of state)" % (cells * 56 * 2 / 1e6),
+                       "diag_every": params[0]["diag_every"]},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind
+                         if peak_kind == "measured" else "fallback 6.8 TB/s",
+                         "kernel": "step_kernel", "launches": k_launches,
+                         "ms_per_launch": per_launch_ms,
+                         "algorithmic_bytes_per_launch": BYTES_PER_LUP * launch_cells},
+            "e2e": {"value": e2e_value, "unit": "MLUPS",
+                    "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+                    "scope": "ij_create (params in, lattices initialised) + steps + ij_observe of "
+                             "every lattice's phi and record to host"},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "final_record_lattice0": {k: obs[k] for k in ("step", "mass_n", "breakup_step")},
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(params, args.cpu_seconds)
+        print(json.dumps(line))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=("native", "reference"), default="native")
+    ap.add_argument("--workload", choices=("cfg2", "big", "cfg3"), default="cfg2")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

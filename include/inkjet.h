@@ -1,0 +1,189 @@
+/*
+ * inkjet.h -- C ABI of libinkjet.so, a GB300 (sm_103a) implementation of the
+ * binary-fluid lattice Boltzmann inkjet model of He, Yang, Qin, Wen & Zhang,
+ * "The roles of wettability and surface tension in droplet formation during
+ * inkjet printing" (arXiv:1702.04487).
+ *
+ * The library advances one or more 2-D lattices of the Zheng-Shu-Chew
+ * binary-fluid model (Eq. 1-10, "Methods"): a D2Q9 population f for the mean
+ * density n and momentum, a D2Q5 population g for the order parameter phi,
+ * driven by the time-dependent positive/negative/idle body force of Fig. 1
+ * inside a planar nozzle whose inner wall carries a contact angle ("wetting
+ * boundary condition", Sect. "Reproducing the experiment").
+ *
+ * Conventions for every entry point:
+ *  - All quantities are lattice units (delta x = delta t = 1).
+ *  - Every call returns an ij_status and never aborts the process.
+ *  - Population layout is structure-of-arrays, x fastest: f[i][y][x] with
+ *    i = 0..8 (rest, +x, +y, -x, -y, +x+y, -x+y, -x-y, +x-y) and g[i][y][x]
+ *    with i = 0..4 (the first five of those).  x is the lateral, periodic
+ *    axis (width nx); y is the nozzle axis (height ny), ejection along +y.
+ *  - Device state is owned by the handle; caller buffers are owned by the
+ *    caller and only read or written during the call (or, for *_on_device
+ *    buffers, by work the call enqueues on the handle's stream).
+ *  - Work is enqueued on the CUDA stream given at creation; calls that
+ *    return results to the host synchronise that stream.
+ *  - Numeric failures are per lattice: a lattice whose step met NaN or
+ *    |u| > 0.3 (Mach limit of the lattice) is frozen and reported by
+ *    ij_observe; the other lattices of a batch keep stepping.  Once every
+ *    lattice of a handle is frozen, ij_step returns IJ_ERR_NUMERIC.
+ */
+#ifndef INKJET_H
+#define INKJET_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ij_handle_s* ij_handle;
+
+typedef enum {
+  IJ_OK = 0,
+  IJ_ERR_PARAM = 1,   /* invalid argument; nothing was changed */
+  IJ_ERR_CUDA = 2,    /* a CUDA call failed; see ij_last_error */
+  IJ_ERR_NUMERIC = 3, /* NaN or |u| > 0.3 met in a step of a lattice */
+  IJ_ERR_TIMEOUT = 4, /* reserved: no kernel of this library spins */
+  IJ_ERR_STATE = 5,   /* call not allowed in the handle's state */
+  IJ_ERR_OOM = 6      /* the allocator returned NULL */
+} ij_status;
+
+/* geometry */
+#define IJ_GEOM_NONE 0   /* no solid cells */
+#define IJ_GEOM_NOZZLE 1 /* planar nozzle: channel [cx0, cx0+w), walls of thickness t
+                            on both sides for 0 <= y < L, cx0 = (nx - w) / 2; the
+                            channel-facing wall faces carry the contact angle */
+#define IJ_GEOM_PLATE 2  /* solid rows 0 <= y < t; their top face carries the angle */
+
+/* axial (y) ends */
+#define IJ_BC_ZERO_GRADIENT 0 /* "fully developed": outside rows replicate the edge row */
+#define IJ_BC_PERIODIC 1
+#define IJ_BC_CLOSED 2        /* non-wetting solid rows at y = -1 and y = ny */
+
+/* initial order parameter (n = n0, u = 0, f = f^(0), g = g^(0) everywhere) */
+#define IJ_INIT_MENISCUS 0 /* ink fills the nozzle, flat diffuse meniscus at y = L */
+#define IJ_INIT_DROP 1     /* ink drop of radius init_r at (init_x, init_y) */
+#define IJ_INIT_FLAT 2     /* ink below y = init_y */
+#define IJ_INIT_UNIFORM 3  /* phi = init_r everywhere */
+
+/* population storage */
+#define IJ_FP32 0
+
+typedef struct {
+  int nx, ny;                 /* lattice size, nx, ny >= 1 */
+  int geometry;               /* IJ_GEOM_* */
+  int nozzle_width, nozzle_length, wall_thickness;
+  double rho_ink, rho_air;    /* phi* = (rho_ink - rho_air)/2, n0 = (rho_ink + rho_air)/2 */
+  double nu_ink, nu_air;      /* kinematic viscosities; tau_n = 1/2 + 3 nu(C) */
+  double sigma, width_W;      /* surface tension and interface width (W = 3 in the paper) */
+  double tau_phi, gamma;      /* relaxation time of g (0.8 in the paper) and mobility
+                                 coefficient Gamma; gamma <= 0 selects 0.04 / kappa */
+  double theta_deg;           /* contact angle of the wetting wall faces, degrees */
+  double F0, F_neg;           /* drive: +F0 for T1 steps, -F_neg for T2 steps, then idle */
+  long long T1, T2, T_idle;   /* T_idle > 0 repeats the waveform with period T1+T2+T_idle */
+  int axial_bc;               /* IJ_BC_* */
+  int init_kind;              /* IJ_INIT_* */
+  double init_x, init_y, init_r;
+  double jitter;              /* amplitude of the meniscus jitter (SplitMix64 of seed, x, y) */
+  unsigned long long seed;
+  int diag_every;             /* steps between diagnostics records (0: none) */
+  int precision;              /* IJ_FP32 */
+} ij_params;
+
+/* One diagnostics record, evaluated on the state at time `step` (before
+ * that step's update), in FP64.  Ink weight e = clamp(phi / phi*, 0, 1); row
+ * integrals w(y) = sum_x e; runs are row ranges with w > 1/2.  The neck is the
+ * least w(y) over rows y >= L/2 with more than nozzle_width of run ink above;
+ * breakup is the first record whose neck drops below 0.01, its time
+ * interpolated linearly between records.  The leading droplet is the highest
+ * run. */
+typedef struct {
+  double step;
+  double mass_n, mass_phi;   /* sum of n and phi over fluid cells */
+  double mom_y;              /* sum of n u_y over fluid cells */
+  double neck;
+  double breakup_step;       /* -1 until breakup */
+  double droplet_volume;     /* sum of e over the leading run */
+  double droplet_centroid_y;
+  double droplet_velocity;   /* e n-weighted mean u_y over the leading run */
+  double satellites;         /* runs starting at or above y = L, minus one */
+  double runs;
+  double reserved;
+} ij_obs;
+
+/* Device-memory allocator callbacks; NULL selects cudaMalloc / cudaFree. */
+typedef void* (*ij_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*ij_free_fn)(void* ptr, void* ctx);
+
+/*
+ * ij_create -- build `count` independent lattices (a batch) and initialise
+ * them (n = n0, u = 0, phi from init_kind, mu from phi with the wetting
+ * ghosts, f = f^(0) of Eq. 5-6, g = g^(0) of Eq. 9-10).
+ *   params   : array of `count` parameter blocks (host memory, read only).
+ *   count    : 1 .. 65536.  Lattices may differ in every parameter.
+ *   alloc/free/ctx : device allocator (both NULL or both set).
+ *   stream   : cudaStream_t to enqueue on (NULL: legacy default stream).
+ *   out      : receives the handle.
+ * Errors: IJ_ERR_PARAM (bad sizes or physics: nx, ny < 1, rho_ink <= rho_air,
+ * sigma <= 0, W <= 0, tau_phi <= 0, nu <= 0, nozzle wider than the domain),
+ * IJ_ERR_OOM, IJ_ERR_CUDA.  On error *out is NULL and nothing is leaked.
+ */
+ij_status ij_create(const ij_params* params, int count, ij_alloc_fn alloc, ij_free_fn free_fn,
+                    void* ctx, void* stream, ij_handle* out);
+
+/*
+ * ij_step -- advance every lattice of the handle by nsteps time steps (Eq. 3
+ * for f with the collision of Eq. 4-6, Eq. 8 for g with Eq. 9-10), each step
+ * one fused kernel pass; a diagnostics record is taken at every step t with
+ * t % diag_every == 0.  Asynchronous on the handle's stream.  nsteps >= 0.
+ * Returns IJ_ERR_NUMERIC when every lattice of the handle is frozen (flags are
+ * read without synchronising, so this shows up at most one call late).
+ */
+ij_status ij_step(ij_handle h, long long nsteps);
+
+/*
+ * ij_observe -- synchronise, then return the latest diagnostics record of
+ * lattice `index` in *out (may be NULL) and its order parameter
+ * phi = sum_i g_i (ny*nx floats, solid cells 0) into phi_out (may be NULL;
+ * device pointer if phi_on_device, else host).  Returns IJ_ERR_NUMERIC (with
+ * the outputs filled) if this lattice is frozen by a numeric failure.
+ */
+ij_status ij_observe(ij_handle h, int index, ij_obs* out, float* phi_out, int phi_on_device);
+
+/* ij_history -- copy up to max_records diagnostics records of lattice
+ * `index` (oldest first, 12 doubles each in ij_obs order) into host memory
+ * `out` (may be NULL); *count receives the number of records held. */
+ij_status ij_history(ij_handle h, int index, double* out, int max_records, int* count);
+
+/* ij_get_state / ij_set_state -- copy the populations of lattice `index`
+ * (f: 9*ny*nx floats, g: 5*ny*nx floats, layout above) out of / into the
+ * handle; set_state also sets the time to t.  Host or device buffers. */
+ij_status ij_get_state(ij_handle h, int index, float* f, float* g, int on_device);
+ij_status ij_set_state(ij_handle h, int index, const float* f, const float* g, long long t,
+                       int on_device);
+
+/* ij_time -- current time step of the handle (all lattices share it). */
+ij_status ij_time(ij_handle h, long long* t);
+
+/* ij_launch_count -- number of kernels this handle has launched. */
+ij_status ij_launch_count(ij_handle h, long long* launches);
+
+/* ij_kernel_timing -- measurement aid, no counterpart in the paper.  Reads
+ * (synchronising) the summed duration in ms of the step-kernel launches timed
+ * so far, and their number, into *total_ms / *launches (either may be NULL);
+ * then, if enable >= 0, switches CUDA-event timing of every step-kernel launch
+ * on (1) or off (0) and resets the sums.  Events are recorded on the handle's
+ * stream immediately around each launch. */
+ij_status ij_kernel_timing(ij_handle h, int enable, double* total_ms, long long* launches);
+
+/* ij_destroy -- synchronise and release everything (NULL is accepted). */
+ij_status ij_destroy(ij_handle h);
+
+/* ij_last_error -- message of the last failure on this thread (never NULL). */
+const char* ij_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

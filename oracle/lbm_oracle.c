@@ -580,12 +580,12 @@ void orc_stream_only(orc_sim* s, const double* fin, const double* gin, double* f
  * m(y) = sum_x e n, p(y) = sum_x e n u_y over fluid cells.  Runs: maximal row ranges with w > 1/2.  Neck: the least w(y) over
  * rows y >= y_scan that have more than V_min of run ink (the w of run rows)
  * above them; breakup is the first record whose neck falls below
- * NECK_BREAK (1/20 of a cell of ink: the last thread of ink across the neck
- * row is vanishing), its time interpolated linearly in the neck width
+ * NECK_BREAK (1/100 of a cell of ink: the last thread of ink across the
+ * neck row is vanishing), its time interpolated linearly in the neck width
  * between this record and the previous one.  The leading droplet is the highest run (volume, centroid,
  * e n-weighted velocity); satellites = (runs that start at or above the
  * nozzle exit) - 1. */
-#define NECK_BREAK 0.05
+#define NECK_BREAK 0.01
 
 static void diagnose(orc_sim* s, long long t) {
   int nx = s->nx, ny = s->ny;

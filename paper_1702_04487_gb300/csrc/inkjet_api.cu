@@ -1,0 +1,554 @@
+// Host side of libinkjet.so: parameter validation and derivation, device
+// memory, work lists and launches of the 2-D step (include/inkjet.h).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "inkjet.h"
+#include "lbm2d.cuh"
+
+namespace ij {
+cudaError_t set_step_smem_limit();
+}
+
+using namespace ij;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+ij_status fail(ij_status st, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return st;
+}
+
+#define CUDA_TRY(expr)                                                                     \
+  do {                                                                                     \
+    cudaError_t e_ = (expr);                                                               \
+    if (e_ != cudaSuccess) return fail(IJ_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+  } while (0)
+
+// Contact angle -> wetting potential Omega by bisection on Cahn's relation
+// cos(theta) = ((1 + Omega)^1.5 - (1 - Omega)^1.5) / 2, Omega in [-1, 1].
+double omega_from_theta(double theta_deg) {
+  const double target = cos(theta_deg * M_PI / 180.0);
+  double lo = -1.0, hi = 1.0;
+  for (int it = 0; it < 200; it++) {
+    double mid = 0.5 * (lo + hi);
+    double v = 0.5 * (pow(1.0 + mid, 1.5) - pow(1.0 - mid, 1.5));
+    if (v < target) lo = mid; else hi = mid;
+  }
+  double om = 0.5 * (lo + hi);
+  if (fabs(theta_deg - 90.0) == 0.0) om = 0.0;
+  return om;
+}
+
+struct Bucket {
+  int nthreads;
+  int first, count;  // range in the item array
+  int grid;
+};
+
+}  // namespace
+
+struct ij_handle_s {
+  int n_inst = 0;
+  std::vector<ij_params> params;
+  std::vector<Inst> inst;
+  std::vector<Item> items;
+  std::vector<Bucket> buckets;
+  Inst* d_inst = nullptr;
+  Item* d_items = nullptr;
+  long long* d_t = nullptr;
+  unsigned* d_status = nullptr;  // [n_inst] numeric flags, one per lattice
+  unsigned* h_status = nullptr;  // pinned mirror, refreshed after each ij_step
+  long long t = 0;
+  long long launches = 0;
+  int diag_every = 0;
+  bool poisoned = false;
+  cudaStream_t stream = nullptr;
+  ij_alloc_fn alloc = nullptr;
+  ij_free_fn free_fn = nullptr;
+  void* ctx = nullptr;
+  std::vector<void*> blocks;
+  // optional CUDA-event timing of the step-kernel launches
+  bool timing = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
+  double timed_ms = 0.0;
+  long long timed_launches = 0;
+  cudaEvent_t get_event() {
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  void drain_events() {
+    for (auto& pr : events) {
+      float ms = 0.0f;
+      if (cudaEventSynchronize(pr.second) == cudaSuccess &&
+          cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess)
+        timed_ms += ms;
+      cudaEventDestroy(pr.first);
+      cudaEventDestroy(pr.second);
+    }
+    events.clear();
+  }
+
+  void* dalloc(size_t bytes) {
+    bytes = (bytes + 255) & ~(size_t)255;
+    void* p = nullptr;
+    if (alloc) {
+      p = alloc(bytes, ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      p = nullptr;
+    }
+    if (p) blocks.push_back(p);
+    return p;
+  }
+  void release() {
+    if (stream) cudaStreamSynchronize(stream); else cudaDeviceSynchronize();
+    drain_events();
+    for (void* p : blocks) {
+      if (free_fn) free_fn(p, ctx); else cudaFree(p);
+    }
+    blocks.clear();
+    if (h_status) cudaFreeHost(h_status);
+    h_status = nullptr;
+  }
+};
+
+namespace {
+
+ij_status validate(const ij_params& p, int k) {
+  if (p.nx < 1 || p.ny < 1) return fail(IJ_ERR_PARAM, "lattice %d: nx, ny must be >= 1", k);
+  if ((long long)p.nx * p.ny > (1LL << 31) / 9)
+    return fail(IJ_ERR_PARAM, "lattice %d: nx*ny too large for 32-bit plane indexing", k);
+  if (!(p.rho_ink > p.rho_air) || !(p.rho_air > 0))
+    return fail(IJ_ERR_PARAM, "lattice %d: need rho_ink > rho_air > 0", k);
+  if (!(p.sigma > 0) || !(p.width_W > 0) || !(p.tau_phi > 0))
+    return fail(IJ_ERR_PARAM, "lattice %d: sigma, width_W, tau_phi must be > 0", k);
+  if (!(p.nu_ink > 0) || !(p.nu_air > 0))
+    return fail(IJ_ERR_PARAM, "lattice %d: viscosities must be > 0", k);
+  if (!(p.theta_deg >= 0 && p.theta_deg <= 180))
+    return fail(IJ_ERR_PARAM, "lattice %d: theta_deg must be in [0, 180]", k);
+  if (p.geometry < 0 || p.geometry > 2) return fail(IJ_ERR_PARAM, "lattice %d: bad geometry", k);
+  if (p.axial_bc < 0 || p.axial_bc > 2) return fail(IJ_ERR_PARAM, "lattice %d: bad axial_bc", k);
+  if (p.init_kind < 0 || p.init_kind > 3) return fail(IJ_ERR_PARAM, "lattice %d: bad init_kind", k);
+  if (p.precision != IJ_FP32) return fail(IJ_ERR_PARAM, "lattice %d: unsupported precision", k);
+  if (p.T1 < 0 || p.T2 < 0 || p.T_idle < 0) return fail(IJ_ERR_PARAM, "lattice %d: negative durations", k);
+  if (p.diag_every < 0) return fail(IJ_ERR_PARAM, "lattice %d: diag_every < 0", k);
+  if (p.geometry == IJ_GEOM_NOZZLE) {
+    if (p.nozzle_width < 1 || p.wall_thickness < 1 || p.nozzle_length < 0 ||
+        p.nozzle_width + 2 * p.wall_thickness > p.nx)
+      return fail(IJ_ERR_PARAM, "lattice %d: nozzle (width + 2 walls) must fit in nx", k);
+  }
+  if (p.geometry == IJ_GEOM_PLATE && (p.wall_thickness < 1 || p.wall_thickness >= p.ny))
+    return fail(IJ_ERR_PARAM, "lattice %d: plate thickness must be in [1, ny)", k);
+  return IJ_OK;
+}
+
+// Derived constants of one lattice (free energy, relaxation, wetting).
+Inst derive(const ij_params& p) {
+  Inst I;
+  memset(&I, 0, sizeof(I));
+  I.nx = p.nx;
+  I.ny = p.ny;
+  I.geom = p.geometry;
+  I.cx0 = (p.nx - p.nozzle_width) / 2;
+  I.cx1 = I.cx0 + p.nozzle_width;
+  I.L = p.nozzle_length;
+  I.wt = p.wall_thickness;
+  I.bc = p.axial_bc;
+  I.init_kind = p.init_kind;
+  const double phis = 0.5 * (p.rho_ink - p.rho_air), n0 = 0.5 * (p.rho_ink + p.rho_air);
+  const double A = 3.0 * p.sigma / (8.0 * p.width_W * phis * phis * phis * phis);
+  const double kappa = 3.0 * p.sigma * p.width_W / (4.0 * phis * phis);
+  const double q = 1.0 / (p.tau_phi + 0.5);
+  const double gamma = p.gamma > 0 ? p.gamma : 0.04 / kappa;
+  const double h = omega_from_theta(p.theta_deg) * phis * phis * sqrt(2.0 * kappa * A);
+  I.phis = (float)phis;
+  I.inv_phis = (float)(1.0 / phis);
+  I.A4 = (float)(4.0 * A);
+  I.kappa = (float)kappa;
+  I.hk = (float)(h / kappa);
+  I.q = (float)q;
+  I.omq = 1.0f - I.q;  // exact in FP32 (q in [1/2, 1]), so (1-q) + q == 1 there too
+  I.n0 = (float)n0;
+  I.inv_tphi = (float)(1.0 / p.tau_phi);
+  I.gamma = (float)gamma;
+  I.inv2q = (float)(1.0 / (2.0 * q));
+  I.nu_air = (float)p.nu_air;
+  I.dnu = (float)(p.nu_ink - p.nu_air);
+  I.F0 = (float)p.F0;
+  I.Fneg = (float)p.F_neg;
+  I.T1 = p.T1;
+  I.T2 = p.T2;
+  I.Tidle = p.T_idle;
+  I.d_phis = phis;
+  I.d_n0 = n0;
+  I.d_A = A;
+  I.d_kappa = kappa;
+  I.d_h = h;
+  I.d_gamma = gamma;
+  I.d_q = q;
+  I.d_W = p.width_W;
+  I.init_x = p.init_x;
+  I.init_y = p.init_y;
+  I.init_r = p.init_r;
+  I.jitter = p.jitter;
+  I.seed = p.seed;
+  const bool nozzle = p.geometry == IJ_GEOM_NOZZLE;
+  I.y_exit = nozzle ? p.nozzle_length : 0;
+  I.y_scan = nozzle ? p.nozzle_length - p.nozzle_length / 2 : 0;
+  I.vmin = nozzle ? (double)p.nozzle_width : 1.0;
+  return I;
+}
+
+// Work list: strips of columns x chunks of rows, grouped by block size.
+void build_items(ij_handle h, int chunk) {
+  std::vector<std::pair<int, Item>> all;
+  for (int k = 0; k < h->n_inst; k++) {
+    const Inst& I = h->inst[k];
+    int nt, wc, single, nstrip, stride;
+    if (I.nx <= 256) {
+      nt = (I.nx + 31) / 32 * 32;
+      wc = I.nx;
+      single = 1;
+      nstrip = 1;
+      stride = 0;
+    } else {
+      nt = 256;
+      wc = nt;
+      single = 0;
+      stride = nt - 2;
+      nstrip = (I.nx + stride - 1) / stride;
+    }
+    for (int s = 0; s < nstrip; s++)
+      for (int y0 = 0; y0 < I.ny; y0 += chunk) {
+        Item it;
+        it.inst = k;
+        it.xs = single ? 0 : s * stride - 1;
+        it.wc = wc;
+        it.single = single;
+        it.y0 = y0;
+        it.ch = std::min(chunk, I.ny - y0);
+        all.push_back({nt, it});
+      }
+  }
+  std::stable_sort(all.begin(), all.end(),
+                   [](const std::pair<int, Item>& a, const std::pair<int, Item>& b) { return a.first < b.first; });
+  h->items.clear();
+  h->buckets.clear();
+  for (size_t i = 0; i < all.size(); i++) {
+    if (h->buckets.empty() || h->buckets.back().nthreads != all[i].first)
+      h->buckets.push_back(Bucket{all[i].first, (int)i, 0, 0});
+    h->buckets.back().count++;
+    h->items.push_back(all[i].second);
+  }
+  for (Bucket& b : h->buckets) b.grid = b.count;
+}
+
+ij_status check_handle(ij_handle h) {
+  if (!h) return fail(IJ_ERR_PARAM, "null handle");
+  return IJ_OK;
+}
+
+ij_status one_step(ij_handle h) {
+  const bool diag = h->diag_every > 0 && h->t % h->diag_every == 0;
+  for (const Bucket& b : h->buckets) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (h->timing) {
+      e0 = h->get_event();
+      e1 = h->get_event();
+      CUDA_TRY(cudaEventRecord(e0, h->stream));
+    }
+    CUDA_TRY(launch_step(h->d_inst, h->d_items + b.first, b.count, b.nthreads, b.grid, h->d_t, 0,
+                         diag, h->stream));
+    h->launches++;
+    if (h->timing) {
+      CUDA_TRY(cudaEventRecord(e1, h->stream));
+      h->events.push_back({e0, e1});
+      h->timed_launches++;
+    }
+  }
+  if (diag) {
+    CUDA_TRY(launch_finalize(h->d_inst, h->n_inst, h->d_t, h->stream));
+    h->launches++;
+  }
+  CUDA_TRY(launch_advance(h->d_t, 1, h->stream));
+  h->launches++;
+  h->t++;
+  return IJ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ij_status ij_create(const ij_params* params, int count, ij_alloc_fn alloc, ij_free_fn free_fn,
+                    void* ctx, void* stream, ij_handle* out) {
+  if (!out) return fail(IJ_ERR_PARAM, "out is NULL");
+  *out = nullptr;
+  if (!params || count < 1 || count > 65536) return fail(IJ_ERR_PARAM, "count must be in [1, 65536]");
+  if ((alloc == nullptr) != (free_fn == nullptr))
+    return fail(IJ_ERR_PARAM, "alloc and free callbacks must be both set or both NULL");
+  int de = params[0].diag_every;
+  for (int k = 0; k < count; k++) {
+    ij_status st = validate(params[k], k);
+    if (st != IJ_OK) return st;
+    if (params[k].diag_every != de)
+      return fail(IJ_ERR_PARAM, "all lattices of a batch must share diag_every");
+  }
+  ij_handle h = new (std::nothrow) ij_handle_s();
+  if (!h) return fail(IJ_ERR_OOM, "host allocation failed");
+  h->n_inst = count;
+  h->params.assign(params, params + count);
+  h->stream = (cudaStream_t)stream;
+  h->alloc = alloc;
+  h->free_fn = free_fn;
+  h->ctx = ctx;
+  h->diag_every = de;
+  auto bail = [&](ij_status st) {
+    h->release();
+    delete h;
+    return st;
+  };
+  cudaError_t e = set_step_smem_limit();
+  if (e != cudaSuccess) return bail(fail(IJ_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e)));
+  h->inst.resize(count);
+  for (int k = 0; k < count; k++) {
+    Inst I = derive(params[k]);
+    const size_t N = (size_t)I.nx * I.ny;
+    for (int b = 0; b < 2; b++) {
+      I.f[b] = (float*)h->dalloc(9 * N * sizeof(float));
+      I.g[b] = (float*)h->dalloc(5 * N * sizeof(float));
+      if (!I.f[b] || !I.g[b]) return bail(fail(IJ_ERR_OOM, "device allocation of lattice %d failed", k));
+    }
+    I.rows = (double*)h->dalloc(3 * (size_t)I.ny * sizeof(double));
+    I.sums = (double*)h->dalloc(4 * sizeof(double));
+    I.hist = (double*)h->dalloc((size_t)kHistCap * kRec * sizeof(double));
+    I.dstate = (double*)h->dalloc(8 * sizeof(double));
+    if (!I.rows || !I.sums || !I.hist || !I.dstate)
+      return bail(fail(IJ_ERR_OOM, "device allocation of diagnostics failed"));
+    h->inst[k] = I;
+  }
+  build_items(h, 32);
+  h->d_inst = (Inst*)h->dalloc(count * sizeof(Inst));
+  h->d_items = (Item*)h->dalloc(h->items.size() * sizeof(Item));
+  h->d_t = (long long*)h->dalloc(sizeof(long long));
+  h->d_status = (unsigned*)h->dalloc(count * sizeof(unsigned));
+  for (int k = 0; k < count && h->d_status; k++) h->inst[k].status = h->d_status + k;
+  if (!h->d_inst || !h->d_items || !h->d_t || !h->d_status)
+    return bail(fail(IJ_ERR_OOM, "device allocation of descriptors failed"));
+  if (cudaMallocHost((void**)&h->h_status, count * sizeof(unsigned)) != cudaSuccess)
+    return bail(fail(IJ_ERR_OOM, "pinned allocation failed"));
+  memset(h->h_status, 0, count * sizeof(unsigned));
+  cudaStream_t s = h->stream;
+#define BAIL_CUDA(expr)                                                                       \
+  do {                                                                                        \
+    cudaError_t e_ = (expr);                                                                  \
+    if (e_ != cudaSuccess) return bail(fail(IJ_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(e_))); \
+  } while (0)
+  BAIL_CUDA(cudaMemcpyAsync(h->d_inst, h->inst.data(), count * sizeof(Inst), cudaMemcpyHostToDevice, s));
+  BAIL_CUDA(cudaMemcpyAsync(h->d_items, h->items.data(), h->items.size() * sizeof(Item),
+                            cudaMemcpyHostToDevice, s));
+  BAIL_CUDA(cudaMemsetAsync(h->d_t, 0, sizeof(long long), s));
+  BAIL_CUDA(cudaMemsetAsync(h->d_status, 0, count * sizeof(unsigned), s));
+  const double dinit[8] = {0, 0, 0, -1, 0, 0, 0, 0};
+  for (int k = 0; k < count; k++) {
+    const Inst& I = h->inst[k];
+    BAIL_CUDA(cudaMemsetAsync(I.rows, 0, 3 * (size_t)I.ny * sizeof(double), s));
+    BAIL_CUDA(cudaMemsetAsync(I.sums, 0, 4 * sizeof(double), s));
+    BAIL_CUDA(cudaMemsetAsync(I.hist, 0, (size_t)kHistCap * kRec * sizeof(double), s));
+    BAIL_CUDA(cudaMemcpyAsync(I.dstate, dinit, sizeof(dinit), cudaMemcpyHostToDevice, s));
+    BAIL_CUDA(launch_init(h->d_inst, I, k, s));
+    h->launches += 4;
+  }
+  BAIL_CUDA(cudaStreamSynchronize(s));
+#undef BAIL_CUDA
+  *out = h;
+  return IJ_OK;
+}
+
+ij_status ij_step(ij_handle h, long long nsteps) {
+  ij_status st = check_handle(h);
+  if (st != IJ_OK) return st;
+  if (nsteps < 0) return fail(IJ_ERR_PARAM, "nsteps < 0");
+  if (!h->poisoned) {
+    int flagged = 0;
+    for (int k = 0; k < h->n_inst; k++) flagged += (h->h_status[k] & kStatusNumeric) != 0;
+    h->poisoned = flagged == h->n_inst;
+  }
+  if (h->poisoned)
+    return fail(IJ_ERR_NUMERIC, "every lattice of the handle has produced NaN or |u| > 0.3");
+  for (long long k = 0; k < nsteps; k++) {
+    st = one_step(h);
+    if (st != IJ_OK) return st;
+  }
+  CUDA_TRY(cudaMemcpyAsync(h->h_status, h->d_status, h->n_inst * sizeof(unsigned),
+                           cudaMemcpyDeviceToHost, h->stream));
+  return IJ_OK;
+}
+
+ij_status ij_observe(ij_handle h, int index, ij_obs* out, float* phi_out, int phi_on_device) {
+  ij_status st = check_handle(h);
+  if (st != IJ_OK) return st;
+  if (index < 0 || index >= h->n_inst) return fail(IJ_ERR_PARAM, "index out of range");
+  const Inst& I = h->inst[index];
+  const size_t N = (size_t)I.nx * I.ny;
+  if (phi_out) {
+    float* dst = phi_on_device ? phi_out : h->inst[index].f[(h->t + 1) & 1];
+    CUDA_TRY(launch_phi(h->d_inst, I, index, h->d_t, dst, h->stream));
+    h->launches++;
+    if (!phi_on_device)
+      CUDA_TRY(cudaMemcpyAsync(phi_out, dst, N * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+  }
+  unsigned status = 0;
+  double dstate[8];
+  CUDA_TRY(cudaMemcpyAsync(&status, h->d_status + index, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                           h->stream));
+  CUDA_TRY(cudaMemcpyAsync(dstate, I.dstate, sizeof(dstate), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  if (out) {
+    long long cnt = (long long)dstate[4];
+    if (cnt <= 0) {
+      memset(out, 0, sizeof(*out));
+      out->step = -1;
+      out->breakup_step = -1;
+    } else {
+      CUDA_TRY(cudaMemcpy(out, I.hist + ((cnt - 1) % kHistCap) * kRec, sizeof(ij_obs),
+                          cudaMemcpyDeviceToHost));
+    }
+  }
+  if (status & kStatusNumeric)
+    return fail(IJ_ERR_NUMERIC, "lattice %d produced NaN or |u| > 0.3 and is frozen", index);
+  return IJ_OK;
+}
+
+ij_status ij_history(ij_handle h, int index, double* out, int max_records, int* count) {
+  ij_status st = check_handle(h);
+  if (st != IJ_OK) return st;
+  if (index < 0 || index >= h->n_inst) return fail(IJ_ERR_PARAM, "index out of range");
+  const Inst& I = h->inst[index];
+  double dstate[8];
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  CUDA_TRY(cudaMemcpy(dstate, I.dstate, sizeof(dstate), cudaMemcpyDeviceToHost));
+  long long cnt = (long long)dstate[4];
+  long long held = std::min<long long>(cnt, kHistCap);
+  if (count) *count = (int)held;
+  if (out && max_records > 0) {
+    long long first = cnt - held;
+    long long n = std::min<long long>(held, max_records);
+    for (long long r = 0; r < n; r++)
+      CUDA_TRY(cudaMemcpy(out + r * kRec, I.hist + ((first + r) % kHistCap) * kRec,
+                          kRec * sizeof(double), cudaMemcpyDeviceToHost));
+  }
+  return IJ_OK;
+}
+
+ij_status ij_get_state(ij_handle h, int index, float* f, float* g, int on_device) {
+  ij_status st = check_handle(h);
+  if (st != IJ_OK) return st;
+  if (index < 0 || index >= h->n_inst) return fail(IJ_ERR_PARAM, "index out of range");
+  const Inst& I = h->inst[index];
+  const size_t N = (size_t)I.nx * I.ny;
+  cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (f) {
+    // the stored deviations become absolute populations on the way out; the
+    // buffer of the other time parity is free between steps and stages them
+    float* stage = on_device ? f : I.f[(h->t + 1) & 1];
+    CUDA_TRY(launch_f_export(h->d_inst, I, index, I.f[h->t & 1], stage, h->stream));
+    h->launches++;
+    if (!on_device)
+      CUDA_TRY(cudaMemcpyAsync(f, stage, 9 * N * sizeof(float), kind, h->stream));
+  }
+  if (g) CUDA_TRY(cudaMemcpyAsync(g, I.g[h->t & 1], 5 * N * sizeof(float), kind, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return IJ_OK;
+}
+
+ij_status ij_set_state(ij_handle h, int index, const float* f, const float* g, long long t,
+                       int on_device) {
+  ij_status st = check_handle(h);
+  if (st != IJ_OK) return st;
+  if (index < 0 || index >= h->n_inst) return fail(IJ_ERR_PARAM, "index out of range");
+  if (t < 0) return fail(IJ_ERR_PARAM, "t < 0");
+  if (h->poisoned) return fail(IJ_ERR_STATE, "handle is poisoned");
+  if (!f || !g) return fail(IJ_ERR_PARAM, "f and g are required");
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  // all lattices share the time: move the others' state to the new parity
+  if ((t & 1) != (h->t & 1)) {
+    for (int k = 0; k < h->n_inst; k++) {
+      if (k == index) continue;
+      const Inst& J = h->inst[k];
+      const size_t M = (size_t)J.nx * J.ny;
+      CUDA_TRY(cudaMemcpyAsync(J.f[t & 1], J.f[h->t & 1], 9 * M * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+      CUDA_TRY(cudaMemcpyAsync(J.g[t & 1], J.g[h->t & 1], 5 * M * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+    }
+  }
+  const Inst& I = h->inst[index];
+  const size_t N = (size_t)I.nx * I.ny;
+  CUDA_TRY(cudaMemcpyAsync(I.f[(t + 1) & 1], f, 9 * N * sizeof(float), kind, h->stream));
+  CUDA_TRY(launch_f_import(h->d_inst, I, index, I.f[(t + 1) & 1], I.f[t & 1], h->stream));
+  h->launches++;
+  CUDA_TRY(cudaMemcpyAsync(I.g[t & 1], g, 5 * N * sizeof(float), kind, h->stream));
+  CUDA_TRY(cudaMemcpyAsync(h->d_t, &t, sizeof(long long), cudaMemcpyHostToDevice, h->stream));
+  const double dinit[8] = {0, 0, 0, -1, 0, 0, 0, 0};
+  for (int k = 0; k < h->n_inst; k++) {
+    const Inst& J = h->inst[k];
+    CUDA_TRY(cudaMemcpyAsync(J.dstate, dinit, sizeof(dinit), cudaMemcpyHostToDevice, h->stream));
+  }
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  h->t = t;
+  return IJ_OK;
+}
+
+ij_status ij_time(ij_handle h, long long* t) {
+  ij_status st = check_handle(h);
+  if (st != IJ_OK) return st;
+  if (!t) return fail(IJ_ERR_PARAM, "t is NULL");
+  *t = h->t;
+  return IJ_OK;
+}
+
+ij_status ij_launch_count(ij_handle h, long long* launches) {
+  ij_status st = check_handle(h);
+  if (st != IJ_OK) return st;
+  if (!launches) return fail(IJ_ERR_PARAM, "launches is NULL");
+  *launches = h->launches;
+  return IJ_OK;
+}
+
+ij_status ij_kernel_timing(ij_handle h, int enable, double* total_ms, long long* launches) {
+  ij_status st = check_handle(h);
+  if (st != IJ_OK) return st;
+  h->drain_events();
+  if (total_ms) *total_ms = h->timed_ms;
+  if (launches) *launches = h->timed_launches;
+  if (enable >= 0) {
+    h->timing = enable != 0;
+    h->timed_ms = 0.0;
+    h->timed_launches = 0;
+  }
+  return IJ_OK;
+}
+
+ij_status ij_destroy(ij_handle h) {
+  if (!h) return IJ_OK;
+  h->release();
+  delete h;
+  return IJ_OK;
+}
+
+const char* ij_last_error(void) { return g_err; }
+
+}  // extern "C"

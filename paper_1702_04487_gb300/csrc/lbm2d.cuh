@@ -1,0 +1,67 @@
+// Internal device-side descriptors of the 2-D binary-fluid LBM step.
+// Shared by the kernels (lbm2d_kernels.cu) and the host API (inkjet_api.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ij {
+
+enum { GEOM_NONE = 0, GEOM_NOZZLE = 1, GEOM_PLATE = 2 };
+enum { BC_ZG = 0, BC_PER = 1, BC_CLOSED = 2 };
+enum { INIT_MENISCUS = 0, INIT_DROP = 1, INIT_FLAT = 2, INIT_UNIFORM = 3 };
+
+constexpr int kRec = 12;        // doubles per diagnostics record
+constexpr int kHistCap = 1024;  // records kept per lattice (ring)
+constexpr int kMaxThreads = 1024;
+constexpr unsigned kStatusNumeric = 1u;
+
+// One lattice.  FP32 constants feed the step kernel; FP64 ones the
+// initialisation and the diagnostics.
+struct Inst {
+  int nx, ny, geom, cx0, cx1, L, wt, bc;
+  int y_exit, y_scan, init_kind, pad0;
+  // step constants (FP32)
+  float phis, inv_phis, A4, kappa, hk, q, omq, inv_tphi, gamma, inv2q, nu_air, dnu, F0, Fneg;
+  float n0;  // rest density: f is stored as the deviation f_i - w_i n0
+  long long T1, T2, Tidle;
+  // initialisation and diagnostics constants (FP64)
+  double d_phis, d_n0, d_A, d_kappa, d_h, d_gamma, d_q, d_W, init_x, init_y, init_r, jitter, vmin;
+  unsigned long long seed;
+  // populations, double-buffered by time parity: f[t & 1] holds the state at
+  // t.  f holds deviations from the rest equilibrium, f_i - w_i n0, so that
+  // FP32 rounds the small part that varies (about 50x smaller ulp); g is
+  // stored as is.
+  float* f[2];
+  float* g[2];
+  // diagnostics scratch and results
+  double* rows;    // [3][ny]: sum e, sum e n, sum e n u_y per row
+  double* sums;    // [4]: sum n, sum phi, sum n u_y, unused
+  double* hist;    // [kHistCap][kRec] ring of records
+  double* dstate;  // [8]: have_prev, neck_prev, t_prev, breakup, record count
+  unsigned* status;  // this lattice's numeric flag (NaN or |u| > 0.3 seen)
+};
+
+// A unit of work of the step kernel: `ch` rows starting at y0 of a strip of
+// `wc` collision columns starting at column xs (wrapped) of lattice `inst`.
+// single != 0: the strip is the whole periodic width (wc == nx).
+struct Item {
+  int inst, xs, wc, single, y0, ch;
+};
+
+size_t step_smem_bytes(int nthreads);
+
+cudaError_t launch_init(const Inst* d_inst, const Inst& h_inst, int index, cudaStream_t s);
+cudaError_t launch_step(const Inst* d_inst, const Item* d_items, int n_items, int nthreads,
+                        int grid, const long long* d_t, int t_off, bool diag, cudaStream_t s);
+cudaError_t launch_finalize(const Inst* d_inst, int n_inst, const long long* d_t,
+                            cudaStream_t s);
+cudaError_t launch_advance(long long* d_t, int by, cudaStream_t s);
+cudaError_t launch_phi(const Inst* d_inst, const Inst& h_inst, int index, const long long* d_t,
+                       float* out, cudaStream_t s);
+// absolute populations <-> stored deviations (solid cells: 0 <-> 0)
+cudaError_t launch_f_export(const Inst* d_inst, const Inst& h_inst, int index, const float* src,
+                            float* dst, cudaStream_t s);
+cudaError_t launch_f_import(const Inst* d_inst, const Inst& h_inst, int index, const float* src,
+                            float* dst, cudaStream_t s);
+
+}  // namespace ij

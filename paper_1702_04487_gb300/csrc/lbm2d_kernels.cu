@@ -1,0 +1,728 @@
+// Kernels of the 2-D binary-fluid lattice Boltzmann inkjet step
+// (He et al., arXiv:1702.04487, "Methods", Eq. 3-10).
+//
+// Step kernel design (bandwidth-bound stencil, no tensor cores):
+//  - one thread per lattice column; a block owns a strip of columns and a
+//    chunk of rows and marches up the rows, so every cell's populations are
+//    read once and written once per step (structure-of-arrays, coalesced);
+//  - per row iteration, four pipelined stages over shared-memory ring
+//    buffers of three rows: (1) phi = sum g of row R, (2) wetting ghost
+//    values of row R-1, (3) chemical potential, forces, velocity and the
+//    collision of f (Eq. 4-6) and g (Eq. 8-10) on row R-2, (4) streaming of
+//    row R-3 with halfway bounce-back and the stay/move split of Eq. 8;
+//  - geometry is analytic (no mask array) and the x-halo of a strip is
+//    recomputed by its two edge threads;
+//  - diagnostics rows (ink weight, mass, momentum) are reduced in FP64 by
+//    warp shuffles and atomics inside the same pass on diagnostics steps.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "lbm2d.cuh"
+
+namespace ij {
+namespace {
+
+// D2Q9 lattice (Eq. 5-6): rest, +x, +y, -x, -y, +x+y, -x+y, -x-y, +x-y.
+__constant__ int cEX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+__constant__ int cEY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+#define W1 (1.0f / 9.0f)
+#define W2 (1.0f / 36.0f)
+
+__device__ __forceinline__ int wrapi(int v, int m) {
+  int r = v % m;
+  return r < 0 ? r + m : r;
+}
+
+// Axial mapping of a pipeline row; false outside a closed domain.
+__device__ __forceinline__ bool map_row(const Inst& I, int y, int& ym) {
+  if ((unsigned)y < (unsigned)I.ny) {
+    ym = y;
+    return true;
+  }
+  if (I.bc == BC_PER) {
+    ym = wrapi(y, I.ny);
+    return true;
+  }
+  if (I.bc == BC_ZG) {
+    ym = y < 0 ? 0 : I.ny - 1;
+    return true;
+  }
+  return false;
+}
+
+// Kind of an in-domain cell: 0 fluid, 1 solid, 2 solid on a wetting face.
+__device__ __forceinline__ int geom_kind(const Inst& I, int x, int y) {
+  if (I.geom == GEOM_NOZZLE) {
+    if (y < I.L && ((x >= I.cx0 - I.wt && x < I.cx0) || (x >= I.cx1 && x < I.cx1 + I.wt)))
+      return (x == I.cx0 - 1 || x == I.cx1) ? 2 : 1;
+    return 0;
+  }
+  if (I.geom == GEOM_PLATE) {
+    if (y < I.wt) return (y == I.wt - 1) ? 2 : 1;
+    return 0;
+  }
+  return 0;
+}
+
+__device__ __forceinline__ int kind_at(const Inst& I, int x, int y) {
+  int ym;
+  if (!map_row(I, y, ym)) return 1;
+  return geom_kind(I, wrapi(x, I.nx), ym);
+}
+
+// Conservative test: may a fluid cell (x, y) have a solid neighbour?
+__device__ __forceinline__ bool near_solid(const Inst& I, bool colwall, int y) {
+  if (I.bc == BC_CLOSED && (y == 0 || y == I.ny - 1)) return true;
+  if (I.geom == GEOM_NOZZLE) {
+    if (!colwall) return false;
+    if (I.bc == BC_PER && (y == 0 || y == I.ny - 1)) return true;
+    return y - 1 < I.L;
+  }
+  if (I.geom == GEOM_PLATE) {
+    if (I.bc == BC_PER && (y == 0 || y == I.ny - 1)) return true;
+    return y - 1 < I.wt;
+  }
+  return false;
+}
+
+__device__ __forceinline__ bool in_drive(const Inst& I, int x, int ym) {
+  if (I.geom == GEOM_NOZZLE) return x >= I.cx0 && x < I.cx1 && ym < I.L;
+  return true;
+}
+
+// Fig. 1 waveform: +F0, then -F_neg, then idle (periodic if T_idle > 0).
+__device__ __forceinline__ float drive_at(const Inst& I, long long t) {
+  long long tt = t;
+  if (I.Tidle > 0) tt = t % (I.T1 + I.T2 + I.Tidle);
+  if (tt < I.T1) return I.F0;
+  if (tt < I.T1 + I.T2) return -I.Fneg;
+  return 0.0f;
+}
+
+// Wetting ghost value of a solid point from a 3x3 window of phi (centre
+// w[4], rows w[0..2] below, w[6..8] above) and the kinds of its neighbours:
+// the mean over fluid face neighbours of phi + h_s / kappa, else the mean
+// over fluid diagonal neighbours.
+__device__ float ghost_rule(const Inst& I, int kind, int x, int y, const float* w) {
+  float hk = (kind == 2) ? I.hk : 0.0f;
+  const int fx[4] = {1, 0, -1, 0}, fy[4] = {0, 1, 0, -1};
+  float sum = 0.0f;
+  int cnt = 0;
+  for (int d = 0; d < 4; d++)
+    if (kind_at(I, x + fx[d], y + fy[d]) == 0) {
+      sum += w[(fy[d] + 1) * 3 + fx[d] + 1] + hk;
+      cnt++;
+    }
+  if (cnt) return sum / (float)cnt;
+  const int dx[4] = {1, -1, -1, 1}, dy[4] = {1, 1, -1, -1};
+  for (int d = 0; d < 4; d++)
+    if (kind_at(I, x + dx[d], y + dy[d]) == 0) {
+      sum += w[(dy[d] + 1) * 3 + dx[d] + 1];
+      cnt++;
+    }
+  return cnt ? sum / (float)cnt : 0.0f;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// The fused step.  Shared memory per block (NT = blockDim.x):
+//   raw[3][NT+4]  phi of rows (slot = pipeline index mod 3), slot j <-> column xs+j-2
+//   gh [3][NT+2]  phi with ghost values, slot j <-> column xs+j-1
+//   col[3][12][NT] post-collision f_1..8 and moving g parts P_1..4
+//   red[NT/32][6] diagnostics partial sums (FP64)
+template <bool DIAG>
+__global__ void __launch_bounds__(256) step_kernel(const Inst* __restrict__ insts,
+                                                   const Item* __restrict__ items, int n_items,
+                                                   const long long* __restrict__ d_t, int t_off) {
+  extern __shared__ float4 smem4[];
+  float* smem = reinterpret_cast<float*>(smem4);
+  const int NT = blockDim.x;
+  const int c = threadIdx.x;
+  float* raw = smem;
+  float* gh = raw + 3 * (NT + 4);
+  float* col = gh + 3 * (NT + 2);
+  double* red = reinterpret_cast<double*>(col + 36 * NT + (((36 * NT) & 1) ? 1 : 0));
+  const long long t = *d_t + t_off;
+
+  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+    const Item it = items[item];
+    const Inst& I = insts[it.inst];
+    // a lattice whose numeric flag is set is frozen; thread 0 reads the flag
+    // and the barrier-reduction makes the decision uniform across the block
+    if (__syncthreads_or(c == 0 ? (int)*(volatile unsigned*)I.status : 0)) continue;
+    const int nx = I.nx, wc = it.wc, y0 = it.y0, ch = it.ch;
+    const size_t N = (size_t)nx * I.ny;
+    const float* __restrict__ fin = I.f[t & 1];
+    const float* __restrict__ gin = I.g[t & 1];
+    float* __restrict__ fout = I.f[(t + 1) & 1];
+    float* __restrict__ gout = I.g[(t + 1) & 1];
+    const float Fd = drive_at(I, t);
+    const bool active = c < wc;
+    const int x = wrapi(it.xs + c, nx);
+    const bool owned = active && (it.single || (c >= 1 && c <= wc - 2 && it.xs + c < nx));
+    const int xe = (c < 2) ? c : wc + c;  // extra raw slot of threads 0..3
+    const int xex = wrapi(it.xs + xe - 2, nx);
+    const int xg = (c == 0) ? 0 : wc + 1;  // extra ghost slot of threads 0..1
+    const int xgx = wrapi(it.xs + xg - 1, nx);
+    bool colwall = false;
+    if (I.geom == GEOM_NOZZLE) {
+      const int a0 = I.cx0 - I.wt, a1 = I.cx0, b0 = I.cx1, b1 = I.cx1 + I.wt;
+      for (int d = -1; d <= 1; d++) {
+        int xx = wrapi(x + d, nx);
+        colwall |= (xx >= a0 && xx < a1) || (xx >= b0 && xx < b1);
+      }
+    }
+    // rotating per-row state of the own column: rows R, R-1, R-2, R-3
+    float g0[5] = {0, 0, 0, 0, 0}, g1[5] = {0, 0, 0, 0, 0}, g2[5] = {0, 0, 0, 0, 0};
+    int k0 = 1, k1 = 1, k2 = 1, k3 = 1;
+    int m0 = 0, m1 = 0, m2 = 0, m3 = 0;
+    // own post-collision values kept for the next iteration's pull
+    float cf0 = 0.f, cG0 = 0.f, cS[4] = {0.f, 0.f, 0.f, 0.f};
+    double acc_n = 0.0, acc_phi = 0.0, acc_mom = 0.0;
+
+    for (int k = 0; k < ch + 6; k++) {
+      const int R = y0 - 3 + k;
+      const int sR = k % 3, sR1 = (k + 2) % 3, sR2 = (k + 1) % 3;  // rows R, R-1, R-2
+      // ---------------- stage 1: phi of row R; prefetch f of row R-2
+      for (int i = 0; i < 5; i++) {
+        g2[i] = g1[i];
+        g1[i] = g0[i];
+      }
+      k3 = k2;
+      k2 = k1;
+      k1 = k0;
+      m3 = m2;
+      m2 = m1;
+      m1 = m0;
+      {
+        int ym;
+        bool in = map_row(I, R, ym);
+        m0 = ym;
+        k0 = in ? geom_kind(I, x, ym) : 1;
+        float p = 0.0f;
+        if (active && k0 == 0) {
+          const size_t cc = (size_t)ym * nx + x;
+#pragma unroll
+          for (int i = 0; i < 5; i++) {
+            g0[i] = __ldg(gin + i * N + cc);
+            p += g0[i];
+          }
+        }
+        if (active) raw[sR * (NT + 4) + c + 2] = p;
+        if (c < 4) {
+          float pe = 0.0f;
+          if (in && geom_kind(I, xex, ym) == 0) {
+            const size_t cc = (size_t)ym * nx + xex;
+#pragma unroll
+            for (int i = 0; i < 5; i++) pe += __ldg(gin + i * N + cc);
+          }
+          raw[sR * (NT + 4) + xe] = pe;
+        }
+      }
+      float fr[9];
+      const bool do_coll = k >= 4 && active && k2 == 0;
+      if (do_coll) {
+        const size_t cc = (size_t)m2 * nx + x;
+#pragma unroll
+        for (int i = 0; i < 9; i++) fr[i] = __ldg(fin + i * N + cc);
+      }
+      __syncthreads();
+      // ---------------- stage 2: ghost values of row R-1
+      if (k >= 2) {
+        const float* r0 = raw + sR2 * (NT + 4);  // row R-2
+        const float* r1 = raw + sR1 * (NT + 4);  // row R-1
+        const float* r2 = raw + sR * (NT + 4);   // row R
+        float* go = gh + sR1 * (NT + 2);
+        if (active) {
+          const int j = c + 1;
+          float v;
+          if (k1 == 0) {
+            v = r1[j + 1];
+          } else {
+            float w[9] = {r0[j], r0[j + 1], r0[j + 2], r1[j], r1[j + 1], r1[j + 2],
+                          r2[j], r2[j + 1], r2[j + 2]};
+            v = ghost_rule(I, k1, x, R - 1, w);
+          }
+          go[j] = v;
+        }
+        if (c < 2) {
+          const int j = xg;
+          int ym;
+          int kk = map_row(I, R - 1, ym) ? geom_kind(I, xgx, ym) : 1;
+          float v;
+          if (kk == 0) {
+            v = r1[j + 1];
+          } else {
+            float w[9] = {r0[j], r0[j + 1], r0[j + 2], r1[j], r1[j + 1], r1[j + 2],
+                          r2[j], r2[j + 1], r2[j + 2]};
+            v = ghost_rule(I, kk, xgx, R - 1, w);
+          }
+          go[j] = v;
+        }
+      }
+      __syncthreads();
+      // ---------------- stage 3: collision of row R-2
+      const float pf0 = cf0, pG0 = cG0;
+      const float pS0 = cS[0], pS1 = cS[1], pS2 = cS[2], pS3 = cS[3];
+      double dw = 0.0, dm = 0.0, dp = 0.0;
+      if (do_coll) {
+        const int Rc = R - 2;
+        const float* hb = gh + ((k + 0) % 3) * (NT + 2);  // row Rc-1  (pipeline k-3)
+        const float* hc = gh + ((k + 1) % 3) * (NT + 2);  // row Rc    (pipeline k-2)
+        const float* ht = gh + ((k + 2) % 3) * (NT + 2);  // row Rc+1  (pipeline k-1)
+        const int j = c + 1;
+        const float pC = hc[j];
+        const float pE = hc[j + 1], pW = hc[j - 1], pN = ht[j], pS = hb[j];
+        const float pNE = ht[j + 1], pNW = ht[j - 1], pSW = hb[j - 1], pSE = hb[j + 1];
+        const float lap = (2.0f / 3.0f) * (pE + pN + pW + pS) +
+                          (1.0f / 6.0f) * (pNE + pNW + pSW + pSE) - (10.0f / 3.0f) * pC;
+        const float gx = (pE - pW) * (1.0f / 3.0f) + (pNE - pNW - pSW + pSE) * (1.0f / 12.0f);
+        const float gy = (pN - pS) * (1.0f / 3.0f) + (pNE + pNW - pSW - pSE) * (1.0f / 12.0f);
+        float phi = g2[0] + g2[1] + g2[2] + g2[3] + g2[4];
+        const float mu = I.A4 * phi * (phi * phi - I.phis * I.phis) - I.kappa * lap;
+        float C = 0.5f * (phi * I.inv_phis + 1.0f);
+        C = fminf(fmaxf(C, 0.0f), 1.0f);
+        const float Fb = in_drive(I, x, m2) ? Fd * C : 0.0f;
+        const float Fx = mu * gx, Fy = mu * gy + Fb;
+        // fr holds deviations f_i - w_i n0: their sum is n - n0
+        const float dn = fr[0] + fr[1] + fr[2] + fr[3] + fr[4] + fr[5] + fr[6] + fr[7] + fr[8];
+        const float n = I.n0 + dn;
+        const float mx = fr[1] - fr[3] + fr[5] - fr[6] - fr[7] + fr[8];
+        const float my = fr[2] - fr[4] + fr[5] + fr[6] - fr[7] - fr[8];
+        const float inv_n = 1.0f / n;
+        const float ux = (mx + 0.5f * Fx) * inv_n, uy = (my + 0.5f * Fy) * inv_n;
+        const float u2 = ux * ux + uy * uy;
+        if (!(u2 < 0.09f)) atomicOr(I.status, kStatusNumeric);
+        const float tau = 0.5f + 3.0f * (I.nu_air + C * I.dnu);
+        const float om = 1.0f / tau;
+        const float pref = 3.0f * (1.0f - 0.5f * om);
+        // A_i - n0 = 3 (phi mu + n / 3) - n0 for i >= 1 (Eq. 6), on deviations
+        const float p3 = dn + 3.0f * phi * mu;
+        const float uF = ux * Fx + uy * Fy;
+        const float base = -1.5f * u2;  // velocity-independent part of the bracket of Eq. 5
+        // Moving directions first (deviations feq_i - w_i n0); the rest
+        // direction then takes the balance, feq_0 - w_0 n0 = (n - n0) -
+        // sum_{i>=1} (feq_i - w_i n0) and F_0 = -sum_{i>=1} F_i.  This equals
+        // A_0 = 9n/4 - 15 p / 4 of Eq. 6 (the moments of Eq. 5-6 and of the
+        // forcing term are exact) but conserves mass in FP32, whose rounded
+        // weights 4/9, 1/9, 1/36 do not sum to one.
+        float fs[9];
+        float sum_eq = 0.0f, sum_F = 0.0f;
+#pragma unroll
+        for (int i = 1; i < 9; i++) {
+          const float w = i < 5 ? W1 : W2;
+          const float ex = (float)cEX[i], ey = (float)cEY[i];
+          const float cu = ex * ux + ey * uy;
+          const float cF = ex * Fx + ey * Fy;
+          const float feq = w * (p3 + n * (3.0f * cu + 4.5f * cu * cu + base));
+          const float Fi = w * pref * (cF - uF + 3.0f * cu * cF);
+          sum_eq += feq;
+          sum_F += Fi;
+          fs[i] = fr[i] + om * (feq - fr[i]) + Fi;
+        }
+        fs[0] = fr[0] + om * ((dn - sum_eq) - fr[0]) - sum_F;
+        // order parameter: Eq. 9-10 with the rest direction special
+        const float gmu = I.gamma * mu;
+        const float pq = phi * I.inv2q;
+        float* cl = col + ((k + 1) % 3) * 12 * NT;
+#pragma unroll
+        for (int i = 1; i < 9; i++) cl[(i - 1) * NT + c] = fs[i];
+        float sum_ge = 0.0f;
+#pragma unroll
+        for (int i = 1; i < 5; i++) {
+          const float cu = (float)cEX[i] * ux + (float)cEY[i] * uy;
+          const float ge = 0.5f * gmu + pq * cu;
+          sum_ge += ge;
+          const float omi = (ge - g2[i]) * I.inv_tphi;
+          cl[(7 + i) * NT + c] = I.q * g2[i] + omi;
+          cS[i - 1] = I.omq * g2[i];
+        }
+        // rest direction: g0_0 = phi - 2 Gamma mu (Eq. 10), taken as the
+        // balance phi - sum_{i>=1} g0_i so that sum g0 = phi exactly
+        const float om0 = ((phi - sum_ge) - g2[0]) * I.inv_tphi;
+        cf0 = fs[0];
+        cG0 = g2[0] + om0;
+        if (DIAG && owned && Rc >= y0 && Rc < y0 + ch) {
+          float e = fminf(fmaxf(phi * I.inv_phis, 0.0f), 1.0f);
+          dw = (double)e;
+          dm = (double)e * (double)n;
+          dp = dm * (double)uy;
+          acc_n += (double)n;
+          acc_phi += (double)phi;
+          acc_mom += (double)n * (double)uy;
+        }
+      }
+      if (DIAG) {
+        const int Rc = R - 2;
+        if (k >= 4 && Rc >= y0 && Rc < y0 + ch) {
+          dw = warp_sum(dw);
+          dm = warp_sum(dm);
+          dp = warp_sum(dp);
+          if ((c & 31) == 0) {
+            red[(c >> 5) * 3 + 0] = dw;
+            red[(c >> 5) * 3 + 1] = dm;
+            red[(c >> 5) * 3 + 2] = dp;
+          }
+        }
+      }
+      __syncthreads();
+      if (DIAG && c == 0) {
+        const int Rc = R - 2;
+        if (k >= 4 && Rc >= y0 && Rc < y0 + ch) {
+          double sw = 0, sm = 0, sp = 0;
+          for (int wq = 0; wq < (NT + 31) / 32; wq++) {
+            sw += red[wq * 3 + 0];
+            sm += red[wq * 3 + 1];
+            sp += red[wq * 3 + 2];
+          }
+          atomicAdd(I.rows + Rc, sw);
+          atomicAdd(I.rows + I.ny + Rc, sm);
+          atomicAdd(I.rows + 2 * I.ny + Rc, sp);
+        }
+      }
+      // ---------------- stage 4: streaming of row R-3
+      if (k >= 6 && owned && k3 == 0) {
+        const int Y = R - 3;
+        const float* cb = col + ((k + 2) % 3) * 12 * NT;  // row Y-1 (pipeline k-4)
+        const float* cm = col + ((k + 0) % 3) * 12 * NT;  // row Y   (pipeline k-3)
+        const float* ct = col + ((k + 1) % 3) * 12 * NT;  // row Y+1 (pipeline k-2)
+        const int cw = it.single ? (c == 0 ? wc - 1 : c - 1) : c - 1;
+        const int ce = it.single ? (c == wc - 1 ? 0 : c + 1) : c + 1;
+        float fn[9], gn[5];
+        fn[0] = pf0;
+        gn[0] = pG0;
+        // pull f_i(Y) = f*_i(Y - c_i); g_i(Y) = (1-q) g_i(Y) + P_i(Y - c_i)
+        fn[1] = cm[0 * NT + cw];
+        fn[2] = cb[1 * NT + c];
+        fn[3] = cm[2 * NT + ce];
+        fn[4] = ct[3 * NT + c];
+        fn[5] = cb[4 * NT + cw];
+        fn[6] = cb[5 * NT + ce];
+        fn[7] = ct[6 * NT + ce];
+        fn[8] = ct[7 * NT + cw];
+        float P1 = cm[8 * NT + cw], P2 = cb[9 * NT + c], P3 = cm[10 * NT + ce], P4 = ct[11 * NT + c];
+        if (near_solid(I, colwall, Y)) {
+          // halfway bounce-back: a population whose source is solid is the
+          // cell's own post-collision population of the opposite direction
+          const int opp[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+#pragma unroll
+          for (int i = 1; i < 9; i++)
+            if (kind_at(I, x - cEX[i], Y - cEY[i]) != 0) {
+              fn[i] = cm[(opp[i] - 1) * NT + c];
+              if (i == 1) P1 = cm[(8 + 2) * NT + c];
+              if (i == 2) P2 = cm[(8 + 3) * NT + c];
+              if (i == 3) P3 = cm[(8 + 0) * NT + c];
+              if (i == 4) P4 = cm[(8 + 1) * NT + c];
+            }
+        }
+        gn[1] = pS0 + P1;
+        gn[2] = pS1 + P2;
+        gn[3] = pS2 + P3;
+        gn[4] = pS3 + P4;
+        const size_t cc = (size_t)Y * nx + x;
+#pragma unroll
+        for (int i = 0; i < 9; i++) fout[i * N + cc] = fn[i];
+#pragma unroll
+        for (int i = 0; i < 5; i++) gout[i * N + cc] = gn[i];
+      }
+    }
+    if (DIAG) {
+      // lattice sums of this item, one atomic per warp (every lane of the
+      // block takes part; the block size is a multiple of 32)
+      double a = warp_sum(acc_n), b = warp_sum(acc_phi), m = warp_sum(acc_mom);
+      if ((c & 31) == 0) {
+        atomicAdd(I.sums + 0, a);
+        atomicAdd(I.sums + 1, b);
+        atomicAdd(I.sums + 2, m);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Initialisation (FP64): phi_0 of the chosen profile into a temporary.
+__device__ unsigned long long splitmix64(unsigned long long z) {
+  z += 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+__global__ void init_phi_kernel(const Inst* __restrict__ insts, int index, double* phi0) {
+  const Inst& I = insts[index];
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  if (x >= I.nx) return;
+  double v = 0.0;
+  if (geom_kind(I, x, y) == 0) {
+    if (I.init_kind == INIT_MENISCUS) {
+      int dx = max(I.cx0 - x, x - (I.cx1 - 1));
+      if (dx <= 0) {
+        v = I.d_phis * tanh((I.L - y) / I.d_W);
+        if (fabs((double)(y - I.L)) < 2.0 * I.d_W) {
+          unsigned long long ctr = ((unsigned long long)(unsigned)y << 32) | (unsigned)x;
+          unsigned long long r = splitmix64(I.seed ^ splitmix64(ctr));
+          double u = (double)(r >> 11) * (1.0 / 9007199254740992.0);
+          v += I.jitter * (2.0 * u - 1.0);
+        }
+      } else if (y < I.L) {
+        v = -I.d_phis;
+      } else {
+        double dy = (double)(y - I.L);
+        v = I.d_phis * tanh(-sqrt((double)dx * dx + dy * dy) / I.d_W);
+      }
+    } else if (I.init_kind == INIT_DROP) {
+      double ddx = x - I.init_x;
+      ddx -= I.nx * floor(ddx / I.nx + 0.5);
+      double ddy = y - I.init_y;
+      v = I.d_phis * tanh((I.init_r - sqrt(ddx * ddx + ddy * ddy)) / I.d_W);
+    } else if (I.init_kind == INIT_FLAT) {
+      v = I.d_phis * tanh((I.init_y - y) / I.d_W);
+    } else {
+      v = I.init_r;
+    }
+  }
+  phi0[(size_t)y * I.nx + x] = v;
+}
+
+__device__ double phi0_hat(const Inst& I, const double* phi0, int x, int y) {
+  int k = kind_at(I, x, y);
+  int ym = 0;
+  if (k == 0) {
+    map_row(I, y, ym);
+    return phi0[(size_t)ym * I.nx + wrapi(x, I.nx)];
+  }
+  double hk = (k == 2) ? I.d_h / I.d_kappa : 0.0;
+  const int fx[4] = {1, 0, -1, 0}, fy[4] = {0, 1, 0, -1};
+  double sum = 0.0;
+  int cnt = 0;
+  for (int d = 0; d < 4; d++) {
+    int xx = x + fx[d], yy = y + fy[d];
+    if (kind_at(I, xx, yy) == 0) {
+      map_row(I, yy, ym);
+      sum += phi0[(size_t)ym * I.nx + wrapi(xx, I.nx)] + hk;
+      cnt++;
+    }
+  }
+  if (cnt) return sum / cnt;
+  const int dx[4] = {1, -1, -1, 1}, dy[4] = {1, 1, -1, -1};
+  for (int d = 0; d < 4; d++) {
+    int xx = x + dx[d], yy = y + dy[d];
+    if (kind_at(I, xx, yy) == 0) {
+      map_row(I, yy, ym);
+      sum += phi0[(size_t)ym * I.nx + wrapi(xx, I.nx)];
+      cnt++;
+    }
+  }
+  return cnt ? sum / cnt : 0.0;
+}
+
+// f = f^(0)(n0, u = 0), g = g^(0)(u = 0) with mu from phi_0 (FP64).
+__global__ void init_pop_kernel(const Inst* __restrict__ insts, int index, const double* phi0) {
+  const Inst& I = insts[index];
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  if (x >= I.nx) return;
+  const size_t N = (size_t)I.nx * I.ny, cc = (size_t)y * I.nx + x;
+  float* f = I.f[0];  // deviations f_i - w_i n0
+  float* g = I.g[0];
+  if (geom_kind(I, x, y) != 0) {
+    for (int i = 0; i < 9; i++) f[i * N + cc] = 0.0f;
+    for (int i = 0; i < 5; i++) g[i * N + cc] = 0.0f;
+    return;
+  }
+  const double wt[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
+                        1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+  const int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1}, ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+  const double p0 = phi0[cc];
+  double lap = 0.0;
+  for (int i = 1; i < 9; i++) lap += 6.0 * wt[i] * (phi0_hat(I, phi0, x + ex[i], y + ey[i]) - p0);
+  const double mu = 4.0 * I.d_A * p0 * (p0 * p0 - I.d_phis * I.d_phis) - I.d_kappa * lap;
+  const double n = I.d_n0, p = p0 * mu + n / 3.0;
+  for (int i = 0; i < 9; i++) {
+    double Ai = i == 0 ? 2.25 * n - 3.75 * p : 3.0 * p;
+    f[i * N + cc] = (float)(wt[i] * Ai - wt[i] * n);
+  }
+  g[cc] = (float)(p0 - 2.0 * I.d_gamma * mu);
+  for (int i = 1; i < 5; i++) g[i * N + cc] = (float)(0.5 * I.d_gamma * mu);
+}
+
+__global__ void zero_kernel(float* a, size_t n) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  for (; i < n; i += (size_t)gridDim.x * blockDim.x) a[i] = 0.0f;
+}
+
+// ---------------------------------------------------------------------------
+// Diagnostics record (FP64), one block per lattice, one thread does the
+// row scans; the row accumulators are cleared for the next record.
+__global__ void finalize_kernel(const Inst* __restrict__ insts, const long long* d_t) {
+  const Inst& I = insts[blockIdx.x];
+  const int ny = I.ny;
+  double* w = I.rows;
+  double* m = I.rows + ny;
+  double* pr = I.rows + 2 * ny;
+  if (threadIdx.x == 0) {
+    const double t = (double)*d_t;
+    double* st = I.dstate;
+    double neck = 1e30, above = 0.0;
+    for (int y = ny - 1; y >= 0; y--) {
+      if (y >= I.y_scan && above > I.vmin && w[y] < neck) neck = w[y];
+      if (w[y] > 0.5) above += w[y];
+    }
+    const double thr = 0.01;  // neck width at pinch-off, cells of ink
+    if (st[3] < 0.0 && neck < thr) {
+      if (st[0] > 0.0 && st[1] >= thr && st[1] < 1e29)
+        st[3] = st[2] + (t - st[2]) * (st[1] - thr) / (st[1] - neck);
+      else
+        st[3] = t;
+    }
+    st[0] = 1.0;
+    st[1] = neck;
+    st[2] = t;
+    int nruns = 0, nabove = 0, lead0 = -1, lead1 = -1;
+    for (int y = 0; y < ny;) {
+      if (w[y] > 0.5) {
+        int ya = y;
+        while (y < ny && w[y] > 0.5) y++;
+        nruns++;
+        if (ya >= I.y_exit) nabove++;
+        lead0 = ya;
+        lead1 = y;
+      } else {
+        y++;
+      }
+    }
+    double vol = 0, ycm = 0, mm = 0, pp = 0;
+    for (int y = lead0; lead0 >= 0 && y < lead1; y++) {
+      vol += w[y];
+      ycm += y * w[y];
+      mm += m[y];
+      pp += pr[y];
+    }
+    const long long cnt = (long long)st[4];
+    double* rec = I.hist + (cnt % kHistCap) * kRec;
+    rec[0] = t;
+    rec[1] = I.sums[0];
+    rec[2] = I.sums[1];
+    rec[3] = I.sums[2];
+    rec[4] = neck;
+    rec[5] = st[3];
+    rec[6] = vol;
+    rec[7] = vol > 0 ? ycm / vol : 0.0;
+    rec[8] = mm > 0 ? pp / mm : 0.0;
+    rec[9] = nabove > 1 ? nabove - 1 : 0;
+    rec[10] = nruns;
+    rec[11] = 0.0;
+    st[4] = (double)(cnt + 1);
+    I.sums[0] = I.sums[1] = I.sums[2] = I.sums[3] = 0.0;
+  }
+  __syncthreads();
+  for (int y = threadIdx.x; y < 3 * ny; y += blockDim.x) I.rows[y] = 0.0;
+}
+
+__global__ void advance_kernel(long long* d_t, int by) { *d_t += by; }
+
+// phi = sum_i g_i of the current state (solid cells 0).
+__global__ void phi_kernel(const Inst* __restrict__ insts, int index, const long long* d_t,
+                           float* out) {
+  const Inst& I = insts[index];
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  if (x >= I.nx) return;
+  const size_t N = (size_t)I.nx * I.ny, cc = (size_t)y * I.nx + x;
+  const float* g = I.g[*d_t & 1];
+  float p = 0.0f;
+  if (geom_kind(I, x, y) == 0)
+    for (int i = 0; i < 5; i++) p += g[i * N + cc];
+  out[cc] = p;
+}
+
+// Stored deviations <-> absolute populations f_i = dev_i + w_i n0.
+template <bool EXPORT>
+__global__ void f_convert_kernel(const Inst* __restrict__ insts, int index, const float* src,
+                                 float* dst) {
+  const Inst& I = insts[index];
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  if (x >= I.nx) return;
+  const size_t N = (size_t)I.nx * I.ny, cc = (size_t)y * I.nx + x;
+  const bool fluid = geom_kind(I, x, y) == 0;
+  const float wt[9] = {4.0f / 9, 1.0f / 9, 1.0f / 9, 1.0f / 9, 1.0f / 9,
+                       1.0f / 36, 1.0f / 36, 1.0f / 36, 1.0f / 36};
+  for (int i = 0; i < 9; i++) {
+    const float r = wt[i] * I.n0;
+    dst[i * N + cc] = fluid ? (EXPORT ? src[i * N + cc] + r : src[i * N + cc] - r) : 0.0f;
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+size_t step_smem_bytes(int nt) {
+  size_t floats = 3 * (size_t)(nt + 4) + 3 * (size_t)(nt + 2) + 36 * (size_t)nt;
+  floats += floats & 1;
+  return floats * sizeof(float) + (size_t)((nt + 31) / 32) * 3 * sizeof(double);
+}
+
+cudaError_t launch_init(const Inst* d_inst, const Inst& h, int index, cudaStream_t s) {
+  dim3 blk(128), grd((h.nx + 127) / 128, h.ny);
+  double* phi0 = reinterpret_cast<double*>(h.f[1]);  // f[1] is free before the first step
+  init_phi_kernel<<<grd, blk, 0, s>>>(d_inst, index, phi0);
+  init_pop_kernel<<<grd, blk, 0, s>>>(d_inst, index, phi0);
+  const size_t N = (size_t)h.nx * h.ny;
+  zero_kernel<<<256, 256, 0, s>>>(h.f[1], 9 * N);
+  zero_kernel<<<256, 256, 0, s>>>(h.g[1], 5 * N);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step(const Inst* d_inst, const Item* d_items, int n_items, int nthreads,
+                        int grid, const long long* d_t, int t_off, bool diag, cudaStream_t s) {
+  const size_t smem = step_smem_bytes(nthreads);
+  if (diag)
+    step_kernel<true><<<grid, nthreads, smem, s>>>(d_inst, d_items, n_items, d_t, t_off);
+  else
+    step_kernel<false><<<grid, nthreads, smem, s>>>(d_inst, d_items, n_items, d_t, t_off);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const Inst* d_inst, int n_inst, const long long* d_t, cudaStream_t s) {
+  finalize_kernel<<<n_inst, 256, 0, s>>>(d_inst, d_t);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_advance(long long* d_t, int by, cudaStream_t s) {
+  advance_kernel<<<1, 1, 0, s>>>(d_t, by);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_phi(const Inst* d_inst, const Inst& h, int index, const long long* d_t,
+                       float* out, cudaStream_t s) {
+  dim3 blk(128), grd((h.nx + 127) / 128, h.ny);
+  phi_kernel<<<grd, blk, 0, s>>>(d_inst, index, d_t, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_f_export(const Inst* d_inst, const Inst& h, int index, const float* src,
+                            float* dst, cudaStream_t s) {
+  dim3 blk(128), grd((h.nx + 127) / 128, h.ny);
+  f_convert_kernel<true><<<grd, blk, 0, s>>>(d_inst, index, src, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_f_import(const Inst* d_inst, const Inst& h, int index, const float* src,
+                            float* dst, cudaStream_t s) {
+  dim3 blk(128), grd((h.nx + 127) / 128, h.ny);
+  f_convert_kernel<false><<<grd, blk, 0, s>>>(d_inst, index, src, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t set_step_smem_limit() {
+  cudaError_t e = cudaFuncSetAttribute(step_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)step_smem_bytes(kMaxThreads));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(step_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)step_smem_bytes(kMaxThreads));
+}
+
+}  // namespace ij

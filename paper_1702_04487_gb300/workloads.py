@@ -24,9 +24,11 @@ def cfg1(drive="ejecting"):
     viscosities 0.1 / 0.05, inner-wall angle 60 degrees.
 
     ``drive="spec"`` is the nominal waveform (+2e-4 for 800 steps, -1e-4 for
-    400): at this size it only bulges the meniscus (Weber number about 0.9)
-    and never ejects.  ``drive="ejecting"`` raises it to +3.5e-3 for 600 steps
-    then -1.75e-3 for 600 steps, which pinches a droplet off near step 1900.
+    400) at surface tension 0.01: at this size it only bulges the meniscus
+    (Weber number about 0.9) and never ejects.  ``drive="ejecting"`` (the
+    default) lowers the surface tension to 0.0025 and drives +2e-3 for 900
+    steps then -1e-3 for 800 steps: the droplet pinches off near step 3610
+    while the flow stays below |u| = 0.08 (Mach 0.14); run it 4000 steps.
     """
     p = dict(nx=64, ny=256, geometry=GEOM_NOZZLE, nozzle_width=20, nozzle_length=60,
              wall_thickness=4, rho_ink=10.0, rho_air=1.0, nu_ink=0.1, nu_air=0.05,
@@ -36,7 +38,7 @@ def cfg1(drive="ejecting"):
     if drive == "spec":
         p.update(F0=2e-4, F_neg=1e-4, T1=800, T2=400)
     else:
-        p.update(F0=3.5e-3, F_neg=1.75e-3, T1=600, T2=600)
+        p.update(sigma=SIGMA_BASE / 4, F0=2e-3, F_neg=1e-3, T1=900, T2=800)
     return p
 
 
@@ -100,7 +102,7 @@ def small_nozzle(nx=48, ny=96, **kw):
     p = dict(nx=nx, ny=ny, geometry=GEOM_NOZZLE, nozzle_width=16, nozzle_length=30,
              wall_thickness=3, rho_ink=10.0, rho_air=1.0, nu_ink=0.1, nu_air=0.05,
              sigma=SIGMA_BASE, width_W=3.0, tau_phi=0.8, gamma=0.0, theta_deg=60.0,
-             F0=3.5e-3, F_neg=1.75e-3, T1=300, T2=300, T_idle=0, axial_bc=BC_ZERO_GRADIENT,
+             F0=2e-3, F_neg=1e-3, T1=300, T2=300, T_idle=0, axial_bc=BC_ZERO_GRADIENT,
              init_kind=INIT_MENISCUS, jitter=1e-6, seed=1, diag_every=10)
     p.update(kw)
     return p

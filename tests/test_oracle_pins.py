@@ -360,11 +360,12 @@ def test_breakup_rule_agrees_with_connected_components():
     within 40 steps after it."""
     p = W.cfg1()
     s = OracleSim(p)
-    while s.history().shape[0] == 0 or s.history()[-1, 5] < 0:
+    s.step(3400)
+    while s.history()[-1, 5] < 0:
         s.step(10)
-        assert s.t <= 3000
+        assert s.t <= 4000
     tb = s.history()[-1, 5]
-    assert 1800 < tb < 2500
+    assert 3400 < tb < 4000
     s2 = OracleSim(p)
     s2.step(int(tb) - 100)
     assert _components(s2.fields()["phi"] > 0) == 1

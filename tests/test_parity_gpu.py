@@ -1,0 +1,232 @@
+"""Parity of the CUDA step (through the C ABI) with the FP64 oracle.
+
+FP32 on the GPU against FP64 in the oracle: populations are compared
+element by element, scaled by the largest population (f) or phi* (g).  The
+tolerances come from FP32 round-off: one step moves each population through
+about 60 FP32 operations on values of size <= n0, so a single step stays
+within ~1e-6 of the FP64 result; over 1000 steps the dissipative dynamics
+keep the drift of n and phi within 1e-5 relative.
+"""
+import numpy as np
+import pytest
+
+from oracle import OracleSim
+from paper_1702_04487_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ij():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1702_04487_gb300 import inkjet
+    return inkjet
+
+
+def _fields_from_state(f, g):
+    return f.sum(0), g.sum(0)
+
+
+def _rel(a, b, scale):
+    return float(np.abs(np.asarray(a, np.float64) - np.asarray(b, np.float64)).max() / scale)
+
+
+def _one_step_case(ij, p, steps=1, tol=3e-6):
+    """Start both sides from the same (FP32-representable) state, step, and
+    compare every population."""
+    o = OracleSim(p)
+    f0, g0 = o.state()
+    f32, g32 = f0.astype(np.float32), g0.astype(np.float32)
+    o.set_state(f32.astype(np.float64), g32.astype(np.float64), 0)
+    h = ij.ij_create(p)
+    ij.ij_set_state(h, 0, f32, g32, 0)
+    ij.ij_step(h, steps)
+    o.step(steps)
+    fg, gg = ij.ij_get_state(h, 0)
+    fo, go = o.state()
+    sf = np.abs(fo).max()
+    phis = 0.5 * (p["rho_ink"] - p["rho_air"])
+    ef, eg = _rel(fg, fo, sf), _rel(gg, go, phis)
+    assert ef < tol and eg < tol, (ef, eg)
+    return ef, eg
+
+
+def test_initial_state_matches_oracle(ij):
+    for p in (W.cfg1(), W.small_nozzle(), W.small_nozzle(geometry=W.GEOM_PLATE, wall_thickness=3,
+                                                          init_kind=W.INIT_DROP, init_x=20,
+                                                          init_y=10, init_r=8)):
+        h = ij.ij_create(p)
+        fg, gg = ij.ij_get_state(h, 0)
+        fo, go = OracleSim(p).state()
+        assert _rel(fg, fo, np.abs(fo).max()) < 2e-7
+        assert _rel(gg, go, 4.5) < 2e-7
+
+
+def test_one_step_cfg1(ij):
+    _one_step_case(ij, W.cfg1())
+
+
+@pytest.mark.parametrize("bc", [W.BC_ZERO_GRADIENT, W.BC_PERIODIC, W.BC_CLOSED])
+@pytest.mark.parametrize("geom", ["nozzle", "plate", "none"])
+def test_boundaries_and_geometries(ij, bc, geom):
+    kw = dict(axial_bc=bc)
+    if geom == "plate":
+        kw.update(geometry=W.GEOM_PLATE, wall_thickness=3, init_kind=W.INIT_DROP, init_x=20,
+                  init_y=9, init_r=9, theta_deg=50.0)
+    elif geom == "none":
+        kw.update(geometry=W.GEOM_NONE, init_kind=W.INIT_DROP, init_x=10, init_y=40, init_r=8)
+    p = W.small_nozzle(**kw)
+    _one_step_case(ij, p, steps=5, tol=1e-5)
+
+
+@pytest.mark.parametrize("nx,ny", [(37, 53), (1, 7), (5, 2), (3, 1), (300, 41), (513, 19),
+                                   (256, 30), (257, 30)])
+def test_ragged_and_degenerate_sizes(ij, nx, ny):
+    """Widths that are not a multiple of 32, single columns and rows, and
+    widths above one block (several overlapping strips) with a ragged last
+    strip; row chunks with ragged tails."""
+    if nx >= 20:
+        p = W.small_nozzle(nx=nx, ny=ny, nozzle_width=max(4, nx // 4),
+                           nozzle_length=max(1, ny // 3), wall_thickness=2)
+    else:
+        p = W.small_nozzle(nx=nx, ny=ny, geometry=W.GEOM_NONE, init_kind=W.INIT_FLAT,
+                           init_y=ny / 2.0, axial_bc=W.BC_PERIODIC)
+    _one_step_case(ij, p, steps=3, tol=1e-5)
+
+
+def test_cfg1_1000_steps_density_and_order_parameter(ij):
+    """cfg 1 as specified (nominal drive): n and phi after 1000 steps within
+    1e-5 relative L-infinity of the FP64 oracle (scaled by max n and phi*)."""
+    p = W.cfg1(drive="spec")
+    h = ij.ij_create(p)
+    ij.ij_step(h, 1000)
+    fg, gg = ij.ij_get_state(h, 0)
+    o = OracleSim(p)
+    o.step(1000)
+    fo, go = o.state()
+    ng, pg = _fields_from_state(fg.astype(np.float64), gg.astype(np.float64))
+    no, po = _fields_from_state(fo, go)
+    assert _rel(ng, no, np.abs(no).max()) < 1e-5
+    assert _rel(pg, po, 4.5) < 1e-5
+
+
+def test_cfg1_ejecting_1000_steps(ij):
+    """cfg 1 with the ejecting drive: the interface moves at |u| ~ 0.08, so
+    FP32 round-off in u (1.2e-7 relative) displaces it by about
+    |u| eps t = 1e-5 cells over 1000 steps, i.e. |grad phi| ~ 3 times that
+    in phi: the bound on phi is 1e-4 relative to phi*; n stays within 1e-5."""
+    p = W.cfg1()
+    h = ij.ij_create(p)
+    ij.ij_step(h, 1000)
+    fg, gg = ij.ij_get_state(h, 0)
+    o = OracleSim(p)
+    o.step(1000)
+    fo, go = o.state()
+    ng, pg = _fields_from_state(fg.astype(np.float64), gg.astype(np.float64))
+    no, po = _fields_from_state(fo, go)
+    assert _rel(ng, no, np.abs(no).max()) < 1e-5
+    assert _rel(pg, po, 4.5) < 1e-4
+
+
+def test_cfg1_full_run_breakup_and_velocity(ij):
+    """cfg 1 over its 4000-step run: breakup time within 1% and the leading
+    droplet's velocity (just after pinch-off and at the end) within 1% of the
+    oracle's; the diagnostics records agree."""
+    p = W.cfg1()
+    h = ij.ij_create(p)
+    ij.ij_step(h, 4000)
+    obs, phi = ij.ij_observe(h, 0)
+    hist_g = ij.ij_history(h, 0)
+    o = OracleSim(p)
+    o.step(4000)
+    hist_o = o.history()
+    tb = hist_o[-1, 5]
+    assert tb > 0, "oracle run must break up"
+    assert abs(obs["breakup_step"] - tb) <= 0.01 * tb
+    vo = hist_o[-1, 8]
+    assert abs(obs["droplet_velocity"] - vo) <= 0.01 * abs(vo)
+    after = int(np.searchsorted(hist_o[:, 0], tb)) + 1
+    assert abs(hist_g[after, 8] - hist_o[after, 8]) <= 0.01 * abs(hist_o[after, 8])
+    assert hist_g.shape == hist_o.shape
+    assert np.array_equal(hist_g[:, 0], hist_o[:, 0])
+    # masses and volumes track the oracle closely
+    assert np.abs(hist_g[:, 1] - hist_o[:, 1]).max() < 1e-5 * hist_o[0, 1]
+    assert np.abs(hist_g[:, 6] - hist_o[:, 6]).max() < 1e-3 * hist_o[:, 6].max()
+    fo, go = o.state()
+    assert _rel(phi, go.sum(0) * (o.kinds() == 0), 4.5) < 1e-4
+
+
+@pytest.mark.parametrize("bc", [W.BC_PERIODIC, W.BC_CLOSED])
+def test_gpu_mass_drift_is_fp32_roundoff(ij, bc):
+    p = W.small_nozzle(axial_bc=bc, diag_every=50)
+    h = ij.ij_create(p)
+    ij.ij_step(h, 1001)
+    hist = ij.ij_history(h, 0)
+    n0 = hist[0, 1]
+    assert np.abs(hist[:, 1] - n0).max() < 2e-6 * n0
+    assert np.abs(hist[:, 2] - hist[0, 2]).max() < 2e-6 * 4.5 * p["nx"] * p["ny"]
+
+
+def test_batch_of_uneven_lattices_matches_single_runs(ij):
+    """A batch of lattices of different sizes and parameters advances each
+    exactly as it would alone (bitwise: same kernels, same arithmetic)."""
+    ps = W.cfg3_sample(count=5, seed=11)
+    ps = [dict(q, ny=min(q["ny"], 200)) for q in ps]
+    hb = ij.ij_create(ps)
+    ij.ij_step(hb, 20)
+    for k, q in enumerate(ps):
+        h1 = ij.ij_create(q)
+        ij.ij_step(h1, 20)
+        fb, gb = ij.ij_get_state(hb, k)
+        f1, g1 = ij.ij_get_state(h1, 0)
+        assert np.array_equal(fb, f1) and np.array_equal(gb, g1)
+
+
+def test_bench_size_sampled_parity(ij):
+    """The bench workload's lattice (200 x 1600, in the 20-lattice batch that
+    is timed): one instance after 2 steps against the oracle, every cell."""
+    ps = W.cfg2_sweep()
+    hb = ij.ij_create(ps)
+    ij.ij_step(hb, 2)
+    for k in (0, 19):
+        o = OracleSim(ps[k])
+        f0, g0 = o.state()
+        o.set_state(f0.astype(np.float32).astype(np.float64),
+                    g0.astype(np.float32).astype(np.float64), 0)
+        o.step(2)
+        fo, go = o.state()
+        fg, gg = ij.ij_get_state(hb, k)
+        assert _rel(fg, fo, np.abs(fo).max()) < 3e-6
+        assert _rel(gg, go, 4.5) < 3e-6
+
+
+def test_numeric_blowup_is_reported_not_trapped(ij):
+    """An unstable configuration (huge drive) sets the numeric flag; the
+    library returns IJ_ERR_NUMERIC and refuses further steps, and the
+    device stays usable."""
+    p = W.small_nozzle(F0=0.5, T1=10 ** 6)
+    h = ij.ij_create(p)
+    with pytest.raises(ij.InkjetError) as e:
+        for _ in range(50):
+            ij.ij_step(h, 20)
+            ij.ij_observe(h, 0, phi=False)
+    assert e.value.status == ij.IJ_ERR_NUMERIC
+    with pytest.raises(ij.InkjetError):
+        ij.ij_step(h, 1)
+    h2 = ij.ij_create(W.small_nozzle())
+    ij.ij_step(h2, 10)
+    obs, _ = ij.ij_observe(h2, 0)
+
+
+def test_zero_steps_and_bad_index(ij):
+    h = ij.ij_create(W.small_nozzle())
+    f0, g0 = ij.ij_get_state(h, 0)
+    ij.ij_step(h, 0)
+    f1, g1 = ij.ij_get_state(h, 0)
+    assert np.array_equal(f0, f1) and np.array_equal(g0, g1)
+    assert ij.ij_time(h) == 0
+    with pytest.raises(ij.InkjetError):
+        ij.ij_get_state(h, 3)
+    with pytest.raises(ij.InkjetError):
+        ij.ij_step(h, -1)
