@@ -177,6 +177,42 @@ ij_status ij_launch_count(ij_handle h, long long* launches);
  * stream immediately around each launch. */
 ij_status ij_kernel_timing(ij_handle h, int enable, double* total_ms, long long* launches);
 
+/*
+ * ij_step_noalloc -- one time step of ONE lattice between device buffers the
+ * caller owns, allocating nothing (no device memory, no host heap).  The
+ * paper has no counterpart: this is a service for callers that may not
+ * allocate where they step the lattice -- a plugin inside another framework
+ * that owns all device memory through its own pool, a loop that must keep a
+ * fixed memory footprint, or code running while its stream is recorded, where
+ * cudaMalloc is not allowed.  It computes exactly what ij_step computes for a
+ * one-lattice handle.
+ *   params        : the lattice (host memory); nx, ny, geometry as in ij_create.
+ *   t             : time of the input state (selects the drive F(t)).
+ *   f_in, g_in    : device, the state at t.  f holds the stored layout
+ *                   f_i - w_i n0 on fluid cells (n0 = (rho_ink + rho_air)/2,
+ *                   w = 4/9, 1/9, 1/36) and 0 on solid cells; g holds g_i.
+ *                   Same [i][y][x] order as above.  Read only.
+ *   f_out, g_out  : device, receive the state at t+1 (solid cells untouched);
+ *                   must not alias the inputs.
+ *   record_out    : device, 12 doubles (ij_obs order) receiving the
+ *                   diagnostics record of the state at t, or NULL for none.
+ *                   Each call starts a fresh breakup history, so breakup_step
+ *                   is t when the neck is already closed, else -1.
+ *   stream        : cudaStream_t to enqueue on; the call is asynchronous.
+ * Limits: ny <= 8192 and at most 4096 work items (strips of 254 columns times
+ * chunks of 32 rows); larger lattices are rejected with IJ_ERR_PARAM.
+ * Descriptors and scratch live in one fixed device array of about 0.3 MB per
+ * GPU that loads the library, kept until the process exits.  The first call
+ * on a device looks up that array's device address, so make it before any
+ * stream capture.  Every call shares the array: calls whose GPU work
+ * overlaps (for example on two streams) race, so order them on one stream.
+ * The numeric flag is cleared at each call and not reported; NaN shows in the
+ * record.  Errors: IJ_ERR_PARAM, IJ_ERR_CUDA.
+ */
+ij_status ij_step_noalloc(const ij_params* params, long long t, const float* f_in,
+                          const float* g_in, float* f_out, float* g_out, double* record_out,
+                          void* stream);
+
 /* ij_destroy -- synchronise and release everything (NULL is accepted). */
 ij_status ij_destroy(ij_handle h);
 

@@ -291,6 +291,14 @@ ij_status one_step(ij_handle h) {
 
 }  // namespace
 
+namespace ij {
+// Parameter validation and derivation shared with the allocation-free entry
+// point (inkjet_noalloc.cu).
+ij_status validate_params(const ij_params& p, int k) { return validate(p, k); }
+Inst derive_params(const ij_params& p) { return derive(p); }
+ij_status report(ij_status st, const char* msg) { return fail(st, "%s", msg); }
+}  // namespace ij
+
 extern "C" {
 
 ij_status ij_create(const ij_params* params, int count, ij_alloc_fn alloc, ij_free_fn free_fn,

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "inkjet.h"
+
 namespace ij {
 
 enum { GEOM_NONE = 0, GEOM_NOZZLE = 1, GEOM_PLATE = 2 };
@@ -49,6 +51,12 @@ struct Item {
 };
 
 size_t step_smem_bytes(int nthreads);
+cudaError_t set_step_smem_limit();
+
+// host helpers of inkjet_api.cu
+ij_status validate_params(const ij_params& p, int k);
+Inst derive_params(const ij_params& p);
+ij_status report(ij_status st, const char* msg);
 
 cudaError_t launch_init(const Inst* d_inst, const Inst& h_inst, int index, cudaStream_t s);
 cudaError_t launch_step(const Inst* d_inst, const Item* d_items, int n_items, int nthreads,

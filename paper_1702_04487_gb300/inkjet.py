@@ -76,6 +76,7 @@ _sig = {
     "ij_time": [_vp, C.POINTER(_ll)],
     "ij_launch_count": [_vp, C.POINTER(_ll)],
     "ij_kernel_timing": [_vp, _i, _dp, C.POINTER(_ll)],
+    "ij_step_noalloc": [C.POINTER(ij_params), _ll, _fp, _fp, _fp, _fp, _fp, _vp],
     "ij_destroy": [_vp],
 }
 for _name, _args in _sig.items():
