@@ -188,6 +188,7 @@ def run_native(args):
 
     # ---- device-resident throughput
     h = inkjet.ij_create(params)
+    tuning = inkjet.ij_autotune(h, 3) if args.autotune else inkjet.ij_get_tuning(h)
     inkjet.ij_step(h, args.warmup)
     barrier()
     clocks = ClockSampler(local)
@@ -220,6 +221,8 @@ def run_native(args):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     h2 = inkjet.ij_create(params)  # host parameter blocks -> device, initialisation
+    for b in tuning:
+        inkjet.ij_tune(h2, b["block_size"], b["chunk"], b["prefetch"])
     inkjet.ij_step(h2, args.steps)
     phis = [inkjet.ij_observe(h2, k)[1] for k in range(len(params))]  # phi + record -> host
     e1.record(stream)
@@ -250,7 +253,8 @@ def run_native(args):
             "config": {"workload": desc, "lattices": len(params), "cells_per_step": cells,
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (%.0f MB of state)" % (cells * 56 * 2 / 1e6),
-                       "diag_every": params[0]["diag_every"]},
+                       "diag_every": params[0]["diag_every"],
+                       "launch": tuning},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind
@@ -282,6 +286,8 @@ def main():
     ap.add_argument("--impl", choices=("native", "reference"), default="native")
     ap.add_argument("--workload", choices=("cfg2", "big", "cfg3"), default="cfg2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="keep the default launch shape instead of timing candidates first")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     args = ap.parse_args()
     if args.warmup < 3:

@@ -178,6 +178,27 @@ ij_status ij_launch_count(ij_handle h, long long* launches);
 ij_status ij_kernel_timing(ij_handle h, int enable, double* total_ms, long long* launches);
 
 /*
+ * Launch-shape tuning (no counterpart in the paper).  Lattices of a handle
+ * are launched in buckets of equal block size (one thread per column, up to
+ * 256; wider lattices use overlapping 256-column strips).  Each bucket splits
+ * its lattices' rows into chunks of `chunk` rows (one block per strip and
+ * chunk) and stages populations `prefetch` rows (1 or 2) ahead of use.
+ *
+ * ij_tune      -- set chunk and prefetch for the bucket of `block_size`
+ *                 threads (block_size <= 0: every bucket).  Synchronises.
+ * ij_autotune  -- time `reps` trial launches of every candidate (chunks
+ *                 8..192, prefetch 1..2) per bucket on the current state and
+ *                 keep the fastest.  Trial launches leave the state and the
+ *                 time unchanged.  Synchronises.
+ * ij_get_tuning -- block size, chunk, prefetch and item count of bucket
+ *                 `bucket` (0-based); IJ_ERR_PARAM past the last bucket.
+ */
+ij_status ij_tune(ij_handle h, int block_size, int chunk, int prefetch);
+ij_status ij_autotune(ij_handle h, int reps);
+ij_status ij_get_tuning(ij_handle h, int bucket, int* block_size, int* chunk, int* prefetch,
+                        int* items);
+
+/*
  * ij_step_noalloc -- one time step of ONE lattice between device buffers the
  * caller owns, allocating nothing (no device memory, no host heap).  The
  * paper has no counterpart: this is a service for callers that may not

@@ -52,10 +52,13 @@ double omega_from_theta(double theta_deg) {
   return om;
 }
 
+// Lattices launched together: same block size; rows split into chunks of
+// `chunk`, populations staged `prefetch` rows ahead.
 struct Bucket {
   int nthreads;
   int first, count;  // range in the item array
   int grid;
+  int chunk, prefetch;
 };
 
 }  // namespace
@@ -66,6 +69,7 @@ struct ij_handle_s {
   std::vector<Inst> inst;
   std::vector<Item> items;
   std::vector<Bucket> buckets;
+  size_t items_cap = 0;  // capacity of d_items
   Inst* d_inst = nullptr;
   Item* d_items = nullptr;
   long long* d_t = nullptr;
@@ -212,48 +216,66 @@ Inst derive(const ij_params& p) {
   return I;
 }
 
-// Work list: strips of columns x chunks of rows, grouped by block size.
-void build_items(ij_handle h, int chunk) {
-  std::vector<std::pair<int, Item>> all;
-  for (int k = 0; k < h->n_inst; k++) {
-    const Inst& I = h->inst[k];
-    int nt, wc, single, nstrip, stride;
-    if (I.nx <= 256) {
-      nt = (I.nx + 31) / 32 * 32;
-      wc = I.nx;
-      single = 1;
-      nstrip = 1;
-      stride = 0;
-    } else {
-      nt = 256;
-      wc = nt;
-      single = 0;
-      stride = nt - 2;
-      nstrip = (I.nx + stride - 1) / stride;
+// Block size of a lattice: one strip of round_up(nx, 32) threads when nx
+// fits in 256 columns, else overlapping strips of 256 threads.
+int block_size_for(const Inst& I) { return I.nx <= 256 ? (I.nx + 31) / 32 * 32 : 256; }
+
+// Items of one lattice: strips of columns x chunks of rows.
+void lattice_items(const Inst& I, int k, int chunk, std::vector<Item>& out) {
+  const int nt = block_size_for(I);
+  const int single = I.nx <= 256;
+  const int wc = single ? I.nx : nt, stride = single ? 0 : nt - 2;
+  const int nstrip = single ? 1 : (I.nx + stride - 1) / stride;
+  for (int s = 0; s < nstrip; s++)
+    for (int y0 = 0; y0 < I.ny; y0 += chunk) {
+      Item it;
+      it.inst = k;
+      it.xs = single ? 0 : s * stride - 1;
+      it.wc = wc;
+      it.single = single;
+      it.y0 = y0;
+      it.ch = std::min(chunk, I.ny - y0);
+      out.push_back(it);
     }
-    for (int s = 0; s < nstrip; s++)
-      for (int y0 = 0; y0 < I.ny; y0 += chunk) {
-        Item it;
-        it.inst = k;
-        it.xs = single ? 0 : s * stride - 1;
-        it.wc = wc;
-        it.single = single;
-        it.y0 = y0;
-        it.ch = std::min(chunk, I.ny - y0);
-        all.push_back({nt, it});
-      }
-  }
-  std::stable_sort(all.begin(), all.end(),
-                   [](const std::pair<int, Item>& a, const std::pair<int, Item>& b) { return a.first < b.first; });
+}
+
+// Work list grouped by block size; each bucket keeps its chunk and prefetch
+// (defaults: 32 rows, the deepest prefetch that keeps two blocks per SM).
+void build_items(ij_handle h) {
+  std::vector<int> sizes;
+  for (int k = 0; k < h->n_inst; k++) sizes.push_back(block_size_for(h->inst[k]));
+  std::sort(sizes.begin(), sizes.end());
+  sizes.erase(std::unique(sizes.begin(), sizes.end()), sizes.end());
+  std::vector<Bucket> old = h->buckets;
   h->items.clear();
   h->buckets.clear();
-  for (size_t i = 0; i < all.size(); i++) {
-    if (h->buckets.empty() || h->buckets.back().nthreads != all[i].first)
-      h->buckets.push_back(Bucket{all[i].first, (int)i, 0, 0});
-    h->buckets.back().count++;
-    h->items.push_back(all[i].second);
+  for (int nt : sizes) {
+    Bucket b{nt, (int)h->items.size(), 0, 0, 32, step_prefetch_for(nt)};
+    for (const Bucket& o : old)
+      if (o.nthreads == nt) {
+        b.chunk = o.chunk;
+        b.prefetch = o.prefetch;
+      }
+    for (int k = 0; k < h->n_inst; k++)
+      if (block_size_for(h->inst[k]) == nt) lattice_items(h->inst[k], k, b.chunk, h->items);
+    b.count = (int)h->items.size() - b.first;
+    b.grid = b.count;
+    h->buckets.push_back(b);
   }
-  for (Bucket& b : h->buckets) b.grid = b.count;
+}
+
+// Upload the work list, growing the device copy when needed.
+ij_status upload_items(ij_handle h) {
+  if (h->items.size() > h->items_cap) {
+    Item* p = (Item*)h->dalloc(h->items.size() * sizeof(Item));
+    if (!p) return fail(IJ_ERR_OOM, "device allocation of the work list failed");
+    h->d_items = p;  // the old list stays owned by the handle until destroy
+    h->items_cap = h->items.size();
+  }
+  cudaError_t e = cudaMemcpyAsync(h->d_items, h->items.data(), h->items.size() * sizeof(Item),
+                                  cudaMemcpyHostToDevice, h->stream);
+  if (e != cudaSuccess) return fail(IJ_ERR_CUDA, "work list upload: %s", cudaGetErrorString(e));
+  return IJ_OK;
 }
 
 ij_status check_handle(ij_handle h) {
@@ -271,7 +293,7 @@ ij_status one_step(ij_handle h) {
       CUDA_TRY(cudaEventRecord(e0, h->stream));
     }
     CUDA_TRY(launch_step(h->d_inst, h->d_items + b.first, b.count, b.nthreads, b.grid, h->d_t, 0,
-                         diag, h->stream));
+                         diag, b.prefetch, h->stream));
     h->launches++;
     if (h->timing) {
       CUDA_TRY(cudaEventRecord(e1, h->stream));
@@ -348,9 +370,10 @@ ij_status ij_create(const ij_params* params, int count, ij_alloc_fn alloc, ij_fr
       return bail(fail(IJ_ERR_OOM, "device allocation of diagnostics failed"));
     h->inst[k] = I;
   }
-  build_items(h, 32);
+  build_items(h);
   h->d_inst = (Inst*)h->dalloc(count * sizeof(Inst));
   h->d_items = (Item*)h->dalloc(h->items.size() * sizeof(Item));
+  h->items_cap = h->items.size();
   h->d_t = (long long*)h->dalloc(sizeof(long long));
   h->d_status = (unsigned*)h->dalloc(count * sizeof(unsigned));
   for (int k = 0; k < count && h->d_status; k++) h->inst[k].status = h->d_status + k;
@@ -547,6 +570,96 @@ ij_status ij_kernel_timing(ij_handle h, int enable, double* total_ms, long long*
     h->timed_ms = 0.0;
     h->timed_launches = 0;
   }
+  return IJ_OK;
+}
+
+ij_status ij_tune(ij_handle h, int block_size, int chunk, int prefetch) {
+  ij_status st = check_handle(h);
+  if (st != IJ_OK) return st;
+  if (chunk < 1 || (prefetch != 1 && prefetch != 2))
+    return fail(IJ_ERR_PARAM, "chunk must be >= 1 and prefetch 1 or 2");
+  bool found = false;
+  for (Bucket& b : h->buckets)
+    if (block_size <= 0 || b.nthreads == block_size) {
+      if (prefetch > step_prefetch_for(b.nthreads))
+        return fail(IJ_ERR_PARAM, "prefetch %d does not fit two blocks of %d threads per SM",
+                    prefetch, b.nthreads);
+      found = true;
+    }
+  for (Bucket& b : h->buckets)
+    if (block_size <= 0 || b.nthreads == block_size) {
+      b.chunk = chunk;
+      b.prefetch = prefetch;
+    }
+  if (!found) return fail(IJ_ERR_PARAM, "no lattice of the handle runs with %d threads", block_size);
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  build_items(h);
+  return upload_items(h);
+}
+
+ij_status ij_autotune(ij_handle h, int reps) {
+  ij_status st = check_handle(h);
+  if (st != IJ_OK) return st;
+  if (reps < 1) return fail(IJ_ERR_PARAM, "reps must be >= 1");
+  if (h->poisoned) return fail(IJ_ERR_STATE, "handle is poisoned");
+  static const int kChunks[] = {8, 16, 24, 32, 48, 64, 96, 128, 192};
+  cudaEvent_t e0, e1;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  // Trial launches read the state at t and write only the other time buffer
+  // (without diagnostics), so the state is unchanged; t does not advance.
+  for (size_t bi = 0; bi < h->buckets.size(); bi++) {
+    const int nt = h->buckets[bi].nthreads;
+    int max_ny = 1;
+    for (int k = 0; k < h->n_inst; k++)
+      if (block_size_for(h->inst[k]) == nt) max_ny = std::max(max_ny, h->inst[k].ny);
+    float best = 1e30f;
+    int best_chunk = h->buckets[bi].chunk, best_pf = h->buckets[bi].prefetch;
+    for (int pf = 1; pf <= step_prefetch_for(nt); pf++)
+      for (int chunk : kChunks) {
+        if (chunk > 2 * max_ny && chunk != kChunks[0]) continue;
+        h->buckets[bi].chunk = chunk;
+        h->buckets[bi].prefetch = pf;
+        build_items(h);
+        st = upload_items(h);
+        if (st != IJ_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return st; }
+        const Bucket& b = h->buckets[bi];
+        CUDA_TRY(launch_step(h->d_inst, h->d_items + b.first, b.count, nt, b.grid, h->d_t, 0,
+                             false, pf, h->stream));  // warm-up
+        CUDA_TRY(cudaEventRecord(e0, h->stream));
+        for (int r = 0; r < reps; r++)
+          CUDA_TRY(launch_step(h->d_inst, h->d_items + b.first, b.count, nt, b.grid, h->d_t, 0,
+                               false, pf, h->stream));
+        CUDA_TRY(cudaEventRecord(e1, h->stream));
+        CUDA_TRY(cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+        h->launches += reps + 1;
+        if (ms < best) {
+          best = ms;
+          best_chunk = chunk;
+          best_pf = pf;
+        }
+      }
+    h->buckets[bi].chunk = best_chunk;
+    h->buckets[bi].prefetch = best_pf;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  build_items(h);
+  return upload_items(h);
+}
+
+ij_status ij_get_tuning(ij_handle h, int bucket, int* block_size, int* chunk, int* prefetch,
+                        int* items) {
+  ij_status st = check_handle(h);
+  if (st != IJ_OK) return st;
+  if (bucket < 0 || bucket >= (int)h->buckets.size()) return fail(IJ_ERR_PARAM, "no such bucket");
+  const Bucket& b = h->buckets[bucket];
+  if (block_size) *block_size = b.nthreads;
+  if (chunk) *chunk = b.chunk;
+  if (prefetch) *prefetch = b.prefetch;
+  if (items) *items = b.count;
   return IJ_OK;
 }
 

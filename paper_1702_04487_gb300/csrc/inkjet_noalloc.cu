@@ -153,7 +153,8 @@ extern "C" ij_status ij_step_noalloc(const ij_params* params, long long t, const
     NOALLOC_TRY(cudaMemsetAsync(base + kOffSums, 0, 4 * sizeof(double), s));
     NOALLOC_TRY(cudaMemcpyAsync(base + kOffDstate, dinit, sizeof(dinit), cudaMemcpyHostToDevice, s));
   }
-  NOALLOC_TRY(launch_step(d_inst, d_items, (int)n_items, nt, (int)n_items, d_t, 0, diag, s));
+  NOALLOC_TRY(launch_step(d_inst, d_items, (int)n_items, nt, (int)n_items, d_t, 0, diag,
+                          step_prefetch_for(nt), s));
   if (diag) {
     NOALLOC_TRY(launch_finalize(d_inst, 1, d_t, s));
     NOALLOC_TRY(cudaMemcpyAsync(record_out, base + kOffHist, kRec * sizeof(double),

@@ -14,7 +14,7 @@ enum { INIT_MENISCUS = 0, INIT_DROP = 1, INIT_FLAT = 2, INIT_UNIFORM = 3 };
 
 constexpr int kRec = 12;        // doubles per diagnostics record
 constexpr int kHistCap = 1024;  // records kept per lattice (ring)
-constexpr int kMaxThreads = 1024;
+constexpr int kMaxThreads = 256;
 constexpr unsigned kStatusNumeric = 1u;
 
 // One lattice.  FP32 constants feed the step kernel; FP64 ones the
@@ -50,7 +50,7 @@ struct Item {
   int inst, xs, wc, single, y0, ch;
 };
 
-size_t step_smem_bytes(int nthreads);
+size_t step_smem_bytes(int nthreads, int prefetch);
 cudaError_t set_step_smem_limit();
 
 // host helpers of inkjet_api.cu
@@ -60,7 +60,11 @@ ij_status report(ij_status st, const char* msg);
 
 cudaError_t launch_init(const Inst* d_inst, const Inst& h_inst, int index, cudaStream_t s);
 cudaError_t launch_step(const Inst* d_inst, const Item* d_items, int n_items, int nthreads,
-                        int grid, const long long* d_t, int t_off, bool diag, cudaStream_t s);
+                        int grid, const long long* d_t, int t_off, bool diag, int prefetch,
+                        cudaStream_t s);
+// rows staged ahead of use (1 or 2): 2 when two blocks of nthreads still fit
+// one SM's shared memory, else 1
+int step_prefetch_for(int nthreads);
 cudaError_t launch_finalize(const Inst* d_inst, int n_inst, const long long* d_t,
                             cudaStream_t s);
 cudaError_t launch_advance(long long* d_t, int by, cudaStream_t s);

@@ -23,8 +23,13 @@ namespace ij {
 namespace {
 
 // D2Q9 lattice (Eq. 5-6): rest, +x, +y, -x, -y, +x+y, -x+y, -x-y, +x-y.
-__constant__ int cEX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
-__constant__ int cEY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+// Compile-time values, so that products with 0 and +-1 fold away.
+__device__ __forceinline__ constexpr int cEX(int i) {
+  return i == 1 || i == 5 || i == 8 ? 1 : (i == 3 || i == 6 || i == 7 ? -1 : 0);
+}
+__device__ __forceinline__ constexpr int cEY(int i) {
+  return i == 2 || i == 5 || i == 6 ? 1 : (i == 4 || i == 7 || i == 8 ? -1 : 0);
+}
 #define W1 (1.0f / 9.0f)
 #define W2 (1.0f / 36.0f)
 
@@ -103,7 +108,7 @@ __device__ __forceinline__ float drive_at(const Inst& I, long long t) {
 // w[4], rows w[0..2] below, w[6..8] above) and the kinds of its neighbours:
 // the mean over fluid face neighbours of phi + h_s / kappa, else the mean
 // over fluid diagonal neighbours.
-__device__ float ghost_rule(const Inst& I, int kind, int x, int y, const float* w) {
+__device__ __noinline__ float ghost_rule(const Inst& I, int kind, int x, int y, const float* w) {
   float hk = (kind == 2) ? I.hk : 0.0f;
   const int fx[4] = {1, 0, -1, 0}, fy[4] = {0, 1, 0, -1};
   float sum = 0.0f;
@@ -123,29 +128,71 @@ __device__ float ghost_rule(const Inst& I, int kind, int x, int y, const float* 
   return cnt ? sum / (float)cnt : 0.0f;
 }
 
+// Asynchronous 4-byte global -> shared copies (cp.async), grouped per row.
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Bit i set when the source x - c_i, y - c_i of direction i is solid.
+__device__ __noinline__ unsigned solid_sources(const Inst& I, int x, int y) {
+  unsigned m = 0;
+  for (int i = 1; i < 9; i++)
+    if (kind_at(I, x - cEX(i), y - cEY(i)) != 0) m |= 1u << i;
+  return m;
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   return v;
 }
 
+// Kind of the in-domain cell (column kind colk, row ym): 0 fluid, 1 solid,
+// 2 solid on a wetting face.  colk is the kind a nozzle-wall column has below
+// y = L (0 for channel and air columns).
+__device__ __forceinline__ int row_kind(int geom, int colk, int L, int wt, int ym) {
+  if (geom == GEOM_NOZZLE) return ym < L ? colk : 0;
+  if (geom == GEOM_PLATE) return ym < wt ? (ym == wt - 1 ? 2 : 1) : 0;
+  return 0;
+}
+
+__device__ __forceinline__ int column_kind(const Inst& I, int x) {
+  if (I.geom != GEOM_NOZZLE) return 0;
+  if ((x >= I.cx0 - I.wt && x < I.cx0) || (x >= I.cx1 && x < I.cx1 + I.wt))
+    return (x == I.cx0 - 1 || x == I.cx1) ? 2 : 1;
+  return 0;
+}
+
 // ---------------------------------------------------------------------------
-// The fused step.  Shared memory per block (NT = blockDim.x):
-//   raw[3][NT+4]  phi of rows (slot = pipeline index mod 3), slot j <-> column xs+j-2
+// The fused step.  Shared memory per block (NT = blockDim.x, D = P + 3):
+//   ring[D] rows of populations staged by cp.async, P rows ahead of use:
+//           g[5][NT+4] (slot j <-> column xs+j-2) and f[9][NT] (slot c <-> xs+c)
+//   raw[4][NT+4]  phi of rows R..R-3 (ring), slot j <-> column xs+j-2
 //   gh [3][NT+2]  phi with ghost values, slot j <-> column xs+j-1
 //   col[3][12][NT] post-collision f_1..8 and moving g parts P_1..4
-//   red[NT/32][6] diagnostics partial sums (FP64)
-template <bool DIAG>
-__global__ void __launch_bounds__(256) step_kernel(const Inst* __restrict__ insts,
-                                                   const Item* __restrict__ items, int n_items,
-                                                   const long long* __restrict__ d_t, int t_off) {
+//   red[NT/32][3] diagnostics partial sums (FP64)
+template <bool DIAG, int P>
+__global__ void __launch_bounds__(256, 2) step_kernel(const Inst* __restrict__ insts,
+                                                      const Item* __restrict__ items, int n_items,
+                                                      const long long* __restrict__ d_t, int t_off) {
+  constexpr int D = P + 3;
   extern __shared__ float4 smem4[];
   float* smem = reinterpret_cast<float*>(smem4);
   const int NT = blockDim.x;
   const int c = threadIdx.x;
-  float* raw = smem;
-  float* gh = raw + 3 * (NT + 4);
+  const int GW = NT + 4, RS = 5 * GW + 9 * NT;  // g row width, ring slot size (floats)
+  float* ring = smem;
+  float* raw = ring + D * RS;
+  float* gh = raw + 4 * (NT + 4);
   float* col = gh + 3 * (NT + 2);
-  double* red = reinterpret_cast<double*>(col + 36 * NT + (((36 * NT) & 1) ? 1 : 0));
+  double* red = reinterpret_cast<double*>(col + 36 * NT);
   const long long t = *d_t + t_off;
 
   for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
@@ -154,8 +201,22 @@ __global__ void __launch_bounds__(256) step_kernel(const Inst* __restrict__ inst
     // a lattice whose numeric flag is set is frozen; thread 0 reads the flag
     // and the barrier-reduction makes the decision uniform across the block
     if (__syncthreads_or(c == 0 ? (int)*(volatile unsigned*)I.status : 0)) continue;
-    const int nx = I.nx, wc = it.wc, y0 = it.y0, ch = it.ch;
-    const size_t N = (size_t)nx * I.ny;
+    // per-lattice constants in registers
+    const int nx = I.nx, ny = I.ny, geom = I.geom, L = I.L, wt = I.wt, bc = I.bc;
+    const int wc = it.wc, y0 = it.y0, ch = it.ch;
+    const int N = nx * ny;  // < 2^31 / 9 (checked on the host)
+#define phis2 (I.phis * I.phis)
+#define inv_phis (I.inv_phis)
+#define A4 (I.A4)
+#define kappa (I.kappa)
+#define qf (I.q)
+#define omq (I.omq)
+#define inv_tphi (I.inv_tphi)
+#define gamma (I.gamma)
+#define inv2q (I.inv2q)
+#define nu_air (I.nu_air)
+#define dnu (I.dnu)
+#define n0 (I.n0)
     const float* __restrict__ fin = I.f[t & 1];
     const float* __restrict__ gin = I.g[t & 1];
     float* __restrict__ fout = I.f[(t + 1) & 1];
@@ -168,83 +229,126 @@ __global__ void __launch_bounds__(256) step_kernel(const Inst* __restrict__ inst
     const int xex = wrapi(it.xs + xe - 2, nx);
     const int xg = (c == 0) ? 0 : wc + 1;  // extra ghost slot of threads 0..1
     const int xgx = wrapi(it.xs + xg - 1, nx);
-    bool colwall = false;
-    if (I.geom == GEOM_NOZZLE) {
-      const int a0 = I.cx0 - I.wt, a1 = I.cx0, b0 = I.cx1, b1 = I.cx1 + I.wt;
-      for (int d = -1; d <= 1; d++) {
-        int xx = wrapi(x + d, nx);
-        colwall |= (xx >= a0 && xx < a1) || (xx >= b0 && xx < b1);
+    const int ck = column_kind(I, x), cke = column_kind(I, xex), ckg = column_kind(I, xgx);
+    const bool drive_col = geom != GEOM_NOZZLE || (x >= I.cx0 && x < I.cx1);
+    // does the strip (with its halo) contain a nozzle-wall column?  Rows with
+    // no solid cell in the strip need no ghost values: their phi is used as is
+    bool strip_wall = false;
+    if (geom == GEOM_NOZZLE) {
+      const int a0 = I.cx0 - I.wt, b1 = I.cx1 + I.wt;
+      if (it.single) {
+        strip_wall = true;
+      } else {
+        for (int j = -2; j < wc + 2 && !strip_wall; j++) {
+          const int xx = wrapi(it.xs + j, nx);
+          strip_wall = xx >= a0 && xx < b1 && column_kind(I, xx) != 0;
+        }
       }
     }
-    // rotating per-row state of the own column: rows R, R-1, R-2, R-3
-    float g0[5] = {0, 0, 0, 0, 0}, g1[5] = {0, 0, 0, 0, 0}, g2[5] = {0, 0, 0, 0, 0};
+    bool colwall = false;
+    if (geom == GEOM_NOZZLE)
+      colwall = ck != 0 || column_kind(I, wrapi(x - 1, nx)) != 0 ||
+                column_kind(I, wrapi(x + 1, nx)) != 0;
+
+    // rotating per-row state of the own column: kinds of rows R..R-3, mapped
+    // rows of R..R-2
     int k0 = 1, k1 = 1, k2 = 1, k3 = 1;
-    int m0 = 0, m1 = 0, m2 = 0, m3 = 0;
+    int m0 = 0, m1 = 0, m2 = 0;
+    // block-uniform: does pipeline row R, R-1, R-2, R-3 hold a solid cell?
+    bool h0 = true, h1 = true, h2 = true, h3 = true;
+    int keR = 1;  // kind of the extra raw column (threads 0..3) in row R
+    // Stage the populations of pipeline row r into ring slot `slot` (own
+    // column; the g halo columns by threads 0..3; f only for rows that are
+    // collided), as one cp.async group.
+    auto stage_row = [&](int r, int slot) {
+      int ym;
+      const bool in = r <= y0 + ch + 2 && map_row(I, r, ym);
+      if (in) {
+        float* sg = ring + slot * RS;
+        const int off = ym * nx;
+        if (active && row_kind(geom, ck, L, wt, ym) == 0) {
+          const float* q = gin + off + x;
+#pragma unroll
+          for (int i = 0; i < 5; i++) cp_async4(sg + i * GW + c + 2, q + i * N);
+          if (r >= y0 - 1 && r <= y0 + ch) {
+            const float* qf_ = fin + off + x;
+            float* sf = sg + 5 * GW;
+#pragma unroll
+            for (int i = 0; i < 9; i++) cp_async4(sf + i * NT + c, qf_ + i * N);
+          }
+        }
+        if (c < 4 && row_kind(geom, cke, L, wt, ym) == 0) {
+          const float* q = gin + off + xex;
+#pragma unroll
+          for (int i = 0; i < 5; i++) cp_async4(sg + i * GW + xe, q + i * N);
+        }
+      }
+      cp_async_commit();
+    };
+    int rs0 = 0;  // ring slot of row R
+#pragma unroll
+    for (int j = 0; j < P; j++) stage_row(y0 - 3 + j, j);
     // own post-collision values kept for the next iteration's pull
-    float cf0 = 0.f, cG0 = 0.f, cS[4] = {0.f, 0.f, 0.f, 0.f};
+    float cf0 = 0.f, cG0 = 0.f, cS0 = 0.f, cS1 = 0.f, cS2 = 0.f, cS3 = 0.f;
     double acc_n = 0.0, acc_phi = 0.0, acc_mom = 0.0;
+    // ring slots of pipeline rows R (s0), R-1 (s1), R-2 (s2) for gh and col;
+    // raw keeps four rows: R (r0), R-1 (r1), R-2 (r2), R-3 (r3)
+    int s0 = 0, s1 = 2, s2 = 1;
+    int r0 = 0, r1 = 3, r2 = 2, r3 = 1;
 
     for (int k = 0; k < ch + 6; k++) {
       const int R = y0 - 3 + k;
-      const int sR = k % 3, sR1 = (k + 2) % 3, sR2 = (k + 1) % 3;  // rows R, R-1, R-2
-      // ---------------- stage 1: phi of row R; prefetch f of row R-2
-      for (int i = 0; i < 5; i++) {
-        g2[i] = g1[i];
-        g1[i] = g0[i];
+      // ---------------- stage 1: phi of row R (staged P iterations ago)
+      {
+        int slot = rs0 + P;
+        if (slot >= D) slot -= D;  // slot of row R+P, last used by row R-3
+        stage_row(R + P, slot);
       }
+      cp_async_wait<P>();  // this thread's copies of row R have landed
       k3 = k2;
       k2 = k1;
       k1 = k0;
-      m3 = m2;
       m2 = m1;
       m1 = m0;
+      h3 = h2;
+      h2 = h1;
+      h1 = h0;
       {
         int ym;
-        bool in = map_row(I, R, ym);
+        const bool in = map_row(I, R, ym);
         m0 = ym;
-        k0 = in ? geom_kind(I, x, ym) : 1;
-        float p = 0.0f;
-        if (active && k0 == 0) {
-          const size_t cc = (size_t)ym * nx + x;
-#pragma unroll
-          for (int i = 0; i < 5; i++) {
-            g0[i] = __ldg(gin + i * N + cc);
-            p += g0[i];
-          }
-        }
-        if (active) raw[sR * (NT + 4) + c + 2] = p;
+        h0 = !in || (geom == GEOM_NOZZLE && strip_wall && ym < L) || (geom == GEOM_PLATE && ym < wt);
+        k0 = in ? row_kind(geom, ck, L, wt, ym) : 1;
+        const float* sg = ring + rs0 * RS;
+        if (active)
+          raw[r0 * (NT + 4) + c + 2] =
+              k0 == 0 ? sg[c + 2] + sg[GW + c + 2] + sg[2 * GW + c + 2] + sg[3 * GW + c + 2] +
+                            sg[4 * GW + c + 2]
+                      : 0.0f;
         if (c < 4) {
-          float pe = 0.0f;
-          if (in && geom_kind(I, xex, ym) == 0) {
-            const size_t cc = (size_t)ym * nx + xex;
-#pragma unroll
-            for (int i = 0; i < 5; i++) pe += __ldg(gin + i * N + cc);
-          }
-          raw[sR * (NT + 4) + xe] = pe;
+          keR = in ? row_kind(geom, cke, L, wt, ym) : 1;
+          raw[r0 * (NT + 4) + xe] =
+              keR == 0 ? sg[xe] + sg[GW + xe] + sg[2 * GW + xe] + sg[3 * GW + xe] + sg[4 * GW + xe]
+                       : 0.0f;
         }
       }
-      float fr[9];
-      const bool do_coll = k >= 4 && active && k2 == 0;
-      if (do_coll) {
-        const size_t cc = (size_t)m2 * nx + x;
-#pragma unroll
-        for (int i = 0; i < 9; i++) fr[i] = __ldg(fin + i * N + cc);
-      }
+      int rs2 = rs0 - 2;  // ring slot of row R-2
+      if (rs2 < 0) rs2 += D;
       __syncthreads();
-      // ---------------- stage 2: ghost values of row R-1
-      if (k >= 2) {
-        const float* r0 = raw + sR2 * (NT + 4);  // row R-2
-        const float* r1 = raw + sR1 * (NT + 4);  // row R-1
-        const float* r2 = raw + sR * (NT + 4);   // row R
-        float* go = gh + sR1 * (NT + 2);
+      // ---------------- stage 2: ghost values of row R-1 (rows with solids)
+      if (k >= 2 && h1) {
+        const float* ra = raw + r2 * (NT + 4);  // row R-2
+        const float* rb = raw + r1 * (NT + 4);  // row R-1
+        const float* rc = raw + r0 * (NT + 4);  // row R
+        float* go = gh + s1 * (NT + 2);
         if (active) {
           const int j = c + 1;
           float v;
           if (k1 == 0) {
-            v = r1[j + 1];
+            v = rb[j + 1];
           } else {
-            float w[9] = {r0[j], r0[j + 1], r0[j + 2], r1[j], r1[j + 1], r1[j + 2],
-                          r2[j], r2[j + 1], r2[j + 2]};
+            float w[9] = {ra[j], ra[j + 1], ra[j + 2], rb[j], rb[j + 1], rb[j + 2],
+                          rc[j], rc[j + 1], rc[j + 2]};
             v = ghost_rule(I, k1, x, R - 1, w);
           }
           go[j] = v;
@@ -252,53 +356,61 @@ __global__ void __launch_bounds__(256) step_kernel(const Inst* __restrict__ inst
         if (c < 2) {
           const int j = xg;
           int ym;
-          int kk = map_row(I, R - 1, ym) ? geom_kind(I, xgx, ym) : 1;
+          const int kk = map_row(I, R - 1, ym) ? row_kind(geom, ckg, L, wt, ym) : 1;
           float v;
           if (kk == 0) {
-            v = r1[j + 1];
+            v = rb[j + 1];
           } else {
-            float w[9] = {r0[j], r0[j + 1], r0[j + 2], r1[j], r1[j + 1], r1[j + 2],
-                          r2[j], r2[j + 1], r2[j + 2]};
+            float w[9] = {ra[j], ra[j + 1], ra[j + 2], rb[j], rb[j + 1], rb[j + 2],
+                          rc[j], rc[j + 1], rc[j + 2]};
             v = ghost_rule(I, kk, xgx, R - 1, w);
           }
           go[j] = v;
         }
+        __syncthreads();
       }
-      __syncthreads();
       // ---------------- stage 3: collision of row R-2
-      const float pf0 = cf0, pG0 = cG0;
-      const float pS0 = cS[0], pS1 = cS[1], pS2 = cS[2], pS3 = cS[3];
+      const float pf0 = cf0, pG0 = cG0, pS0 = cS0, pS1 = cS1, pS2 = cS2, pS3 = cS3;
       double dw = 0.0, dm = 0.0, dp = 0.0;
-      if (do_coll) {
-        const int Rc = R - 2;
-        const float* hb = gh + ((k + 0) % 3) * (NT + 2);  // row Rc-1  (pipeline k-3)
-        const float* hc = gh + ((k + 1) % 3) * (NT + 2);  // row Rc    (pipeline k-2)
-        const float* ht = gh + ((k + 2) % 3) * (NT + 2);  // row Rc+1  (pipeline k-1)
+      const int Rc = R - 2;
+      if (k >= 4 && active && k2 == 0) {
+        const float* sg2 = ring + rs2 * RS;  // g and f of row Rc, own column
+        float g2[5], fr[9];
+#pragma unroll
+        for (int i = 0; i < 5; i++) g2[i] = sg2[i * GW + c + 2];
+#pragma unroll
+        for (int i = 0; i < 9; i++) fr[i] = sg2[5 * GW + i * NT + c];
+        // phi with ghosts of rows Rc-1 (slot of R-3 = slot of R), Rc, Rc+1;
+        // a row without solid cells is read from raw (one column shifted)
+        const float* hb = h3 ? gh + s0 * (NT + 2) : raw + r3 * (NT + 4) + 1;
+        const float* hc = h2 ? gh + s2 * (NT + 2) : raw + r2 * (NT + 4) + 1;
+        const float* ht = h1 ? gh + s1 * (NT + 2) : raw + r1 * (NT + 4) + 1;
         const int j = c + 1;
         const float pC = hc[j];
         const float pE = hc[j + 1], pW = hc[j - 1], pN = ht[j], pS = hb[j];
         const float pNE = ht[j + 1], pNW = ht[j - 1], pSW = hb[j - 1], pSE = hb[j + 1];
-        const float lap = (2.0f / 3.0f) * (pE + pN + pW + pS) +
-                          (1.0f / 6.0f) * (pNE + pNW + pSW + pSE) - (10.0f / 3.0f) * pC;
+        // lap = 6 sum_i w_i (phi_i - phi) from the differences, which are
+        // exact where neighbours are close (no cancellation of O(10) terms)
+        const float lap = (2.0f / 3.0f) * ((pE - pC) + (pN - pC) + (pW - pC) + (pS - pC)) +
+                          (1.0f / 6.0f) * ((pNE - pC) + (pNW - pC) + (pSW - pC) + (pSE - pC));
         const float gx = (pE - pW) * (1.0f / 3.0f) + (pNE - pNW - pSW + pSE) * (1.0f / 12.0f);
         const float gy = (pN - pS) * (1.0f / 3.0f) + (pNE + pNW - pSW - pSE) * (1.0f / 12.0f);
-        float phi = g2[0] + g2[1] + g2[2] + g2[3] + g2[4];
-        const float mu = I.A4 * phi * (phi * phi - I.phis * I.phis) - I.kappa * lap;
-        float C = 0.5f * (phi * I.inv_phis + 1.0f);
+        const float phi = g2[0] + g2[1] + g2[2] + g2[3] + g2[4];
+        const float mu = A4 * phi * ((phi - I.phis) * (phi + I.phis)) - kappa * lap;
+        float C = 0.5f * (phi * inv_phis + 1.0f);
         C = fminf(fmaxf(C, 0.0f), 1.0f);
-        const float Fb = in_drive(I, x, m2) ? Fd * C : 0.0f;
+        const float Fb = (drive_col && m2 < L) || geom != GEOM_NOZZLE ? Fd * C : 0.0f;
         const float Fx = mu * gx, Fy = mu * gy + Fb;
         // fr holds deviations f_i - w_i n0: their sum is n - n0
         const float dn = fr[0] + fr[1] + fr[2] + fr[3] + fr[4] + fr[5] + fr[6] + fr[7] + fr[8];
-        const float n = I.n0 + dn;
+        const float n = n0 + dn;
         const float mx = fr[1] - fr[3] + fr[5] - fr[6] - fr[7] + fr[8];
         const float my = fr[2] - fr[4] + fr[5] + fr[6] - fr[7] - fr[8];
         const float inv_n = 1.0f / n;
         const float ux = (mx + 0.5f * Fx) * inv_n, uy = (my + 0.5f * Fy) * inv_n;
         const float u2 = ux * ux + uy * uy;
         if (!(u2 < 0.09f)) atomicOr(I.status, kStatusNumeric);
-        const float tau = 0.5f + 3.0f * (I.nu_air + C * I.dnu);
-        const float om = 1.0f / tau;
+        const float om = 1.0f / (0.5f + 3.0f * (nu_air + C * dnu));
         const float pref = 3.0f * (1.0f - 0.5f * om);
         // A_i - n0 = 3 (phi mu + n / 3) - n0 for i >= 1 (Eq. 6), on deviations
         const float p3 = dn + 3.0f * phi * mu;
@@ -310,44 +422,62 @@ __global__ void __launch_bounds__(256) step_kernel(const Inst* __restrict__ inst
         // A_0 = 9n/4 - 15 p / 4 of Eq. 6 (the moments of Eq. 5-6 and of the
         // forcing term are exact) but conserves mass in FP32, whose rounded
         // weights 4/9, 1/9, 1/36 do not sum to one.
+        // Opposite directions i, i' share the even part of the equilibrium
+        // and of the forcing term and differ in the sign of the odd part:
+        // feq = E +- O, F = FE +- FO with E = w (p3 + n (base + 4.5 cu^2)),
+        // O = 3 w n cu, FE = w pref (3 cu cF - uF), FO = w pref cF.
         float fs[9];
         float sum_eq = 0.0f, sum_F = 0.0f;
+        const float n3 = 3.0f * n;
 #pragma unroll
         for (int i = 1; i < 9; i++) {
+          if (i == 3 || i == 4 || i == 7 || i == 8) continue;  // handled with its pair
+          const int ib = i == 1 ? 3 : (i == 2 ? 4 : (i == 5 ? 7 : 8));
           const float w = i < 5 ? W1 : W2;
-          const float ex = (float)cEX[i], ey = (float)cEY[i];
+          const float ex = (float)cEX(i), ey = (float)cEY(i);
           const float cu = ex * ux + ey * uy;
           const float cF = ex * Fx + ey * Fy;
-          const float feq = w * (p3 + n * (3.0f * cu + 4.5f * cu * cu + base));
-          const float Fi = w * pref * (cF - uF + 3.0f * cu * cF);
-          sum_eq += feq;
-          sum_F += Fi;
-          fs[i] = fr[i] + om * (feq - fr[i]) + Fi;
+          const float E = w * (p3 + n * (base + 4.5f * cu * cu));
+          const float O = (w * n3) * cu;
+          const float wp = w * pref;
+          const float FE = wp * (3.0f * cu * cF - uF);
+          const float FO = wp * cF;
+          sum_eq += 2.0f * E;
+          sum_F += 2.0f * FE;
+          fs[i] = fr[i] + om * ((E + O) - fr[i]) + (FE + FO);
+          fs[ib] = fr[ib] + om * ((E - O) - fr[ib]) + (FE - FO);
         }
         fs[0] = fr[0] + om * ((dn - sum_eq) - fr[0]) - sum_F;
         // order parameter: Eq. 9-10 with the rest direction special
-        const float gmu = I.gamma * mu;
-        const float pq = phi * I.inv2q;
-        float* cl = col + ((k + 1) % 3) * 12 * NT;
+        const float gmu = gamma * mu;
+        const float pq = phi * inv2q;
+        float* cl = col + s2 * 12 * NT;
 #pragma unroll
         for (int i = 1; i < 9; i++) cl[(i - 1) * NT + c] = fs[i];
         float sum_ge = 0.0f;
+        float S[4];
 #pragma unroll
         for (int i = 1; i < 5; i++) {
-          const float cu = (float)cEX[i] * ux + (float)cEY[i] * uy;
+          const float cu = (float)cEX(i) * ux + (float)cEY(i) * uy;
           const float ge = 0.5f * gmu + pq * cu;
           sum_ge += ge;
-          const float omi = (ge - g2[i]) * I.inv_tphi;
-          cl[(7 + i) * NT + c] = I.q * g2[i] + omi;
-          cS[i - 1] = I.omq * g2[i];
+          const float omi = (ge - g2[i]) * inv_tphi;
+          cl[(7 + i) * NT + c] = qf * g2[i] + omi;
+          S[i - 1] = omq * g2[i];
         }
+        cS0 = S[0];
+        cS1 = S[1];
+        cS2 = S[2];
+        cS3 = S[3];
         // rest direction: g0_0 = phi - 2 Gamma mu (Eq. 10), taken as the
-        // balance phi - sum_{i>=1} g0_i so that sum g0 = phi exactly
-        const float om0 = ((phi - sum_ge) - g2[0]) * I.inv_tphi;
+        // balance phi - sum_{i>=1} g0_i so that sum g0 = phi exactly; with
+        // phi - g_0 = sum_{i>=1} g_i the relaxation uses small terms only
+        // (no difference of two rounded values of size phi*)
+        const float om0 = ((g2[1] + g2[2] + g2[3] + g2[4]) - sum_ge) * inv_tphi;
         cf0 = fs[0];
         cG0 = g2[0] + om0;
         if (DIAG && owned && Rc >= y0 && Rc < y0 + ch) {
-          float e = fminf(fmaxf(phi * I.inv_phis, 0.0f), 1.0f);
+          const float e = fminf(fmaxf(phi * inv_phis, 0.0f), 1.0f);
           dw = (double)e;
           dm = (double)e * (double)n;
           dp = dm * (double)uy;
@@ -356,45 +486,38 @@ __global__ void __launch_bounds__(256) step_kernel(const Inst* __restrict__ inst
           acc_mom += (double)n * (double)uy;
         }
       }
-      if (DIAG) {
-        const int Rc = R - 2;
-        if (k >= 4 && Rc >= y0 && Rc < y0 + ch) {
-          dw = warp_sum(dw);
-          dm = warp_sum(dm);
-          dp = warp_sum(dp);
-          if ((c & 31) == 0) {
-            red[(c >> 5) * 3 + 0] = dw;
-            red[(c >> 5) * 3 + 1] = dm;
-            red[(c >> 5) * 3 + 2] = dp;
-          }
+      if (DIAG && k >= 4 && Rc >= y0 && Rc < y0 + ch) {
+        dw = warp_sum(dw);
+        dm = warp_sum(dm);
+        dp = warp_sum(dp);
+        if ((c & 31) == 0) {
+          red[(c >> 5) * 3 + 0] = dw;
+          red[(c >> 5) * 3 + 1] = dm;
+          red[(c >> 5) * 3 + 2] = dp;
         }
       }
       __syncthreads();
-      if (DIAG && c == 0) {
-        const int Rc = R - 2;
-        if (k >= 4 && Rc >= y0 && Rc < y0 + ch) {
-          double sw = 0, sm = 0, sp = 0;
-          for (int wq = 0; wq < (NT + 31) / 32; wq++) {
-            sw += red[wq * 3 + 0];
-            sm += red[wq * 3 + 1];
-            sp += red[wq * 3 + 2];
-          }
-          atomicAdd(I.rows + Rc, sw);
-          atomicAdd(I.rows + I.ny + Rc, sm);
-          atomicAdd(I.rows + 2 * I.ny + Rc, sp);
+      if (DIAG && c == 0 && k >= 4 && Rc >= y0 && Rc < y0 + ch) {
+        double sw = 0, sm = 0, sp = 0;
+        for (int wq = 0; wq < NT / 32; wq++) {
+          sw += red[wq * 3 + 0];
+          sm += red[wq * 3 + 1];
+          sp += red[wq * 3 + 2];
         }
+        atomicAdd(I.rows + Rc, sw);
+        atomicAdd(I.rows + ny + Rc, sm);
+        atomicAdd(I.rows + 2 * ny + Rc, sp);
       }
       // ---------------- stage 4: streaming of row R-3
       if (k >= 6 && owned && k3 == 0) {
         const int Y = R - 3;
-        const float* cb = col + ((k + 2) % 3) * 12 * NT;  // row Y-1 (pipeline k-4)
-        const float* cm = col + ((k + 0) % 3) * 12 * NT;  // row Y   (pipeline k-3)
-        const float* ct = col + ((k + 1) % 3) * 12 * NT;  // row Y+1 (pipeline k-2)
+        const float* cb = col + s1 * 12 * NT;  // row Y-1 (slot of R-4 = slot of R-1)
+        const float* cm = col + s0 * 12 * NT;  // row Y   (slot of R-3 = slot of R)
+        const float* ct = col + s2 * 12 * NT;  // row Y+1 (slot of R-2)
         const int cw = it.single ? (c == 0 ? wc - 1 : c - 1) : c - 1;
         const int ce = it.single ? (c == wc - 1 ? 0 : c + 1) : c + 1;
-        float fn[9], gn[5];
+        float fn[9];
         fn[0] = pf0;
-        gn[0] = pG0;
         // pull f_i(Y) = f*_i(Y - c_i); g_i(Y) = (1-q) g_i(Y) + P_i(Y - c_i)
         fn[1] = cm[0 * NT + cw];
         fn[2] = cb[1 * NT + c];
@@ -408,28 +531,41 @@ __global__ void __launch_bounds__(256) step_kernel(const Inst* __restrict__ inst
         if (near_solid(I, colwall, Y)) {
           // halfway bounce-back: a population whose source is solid is the
           // cell's own post-collision population of the opposite direction
-          const int opp[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
-#pragma unroll
-          for (int i = 1; i < 9; i++)
-            if (kind_at(I, x - cEX[i], Y - cEY[i]) != 0) {
-              fn[i] = cm[(opp[i] - 1) * NT + c];
-              if (i == 1) P1 = cm[(8 + 2) * NT + c];
-              if (i == 2) P2 = cm[(8 + 3) * NT + c];
-              if (i == 3) P3 = cm[(8 + 0) * NT + c];
-              if (i == 4) P4 = cm[(8 + 1) * NT + c];
-            }
+          const unsigned sm = solid_sources(I, x, Y);
+          if (sm) {
+            if (sm & (1u << 1)) { fn[1] = cm[2 * NT + c]; P1 = cm[10 * NT + c]; }
+            if (sm & (1u << 2)) { fn[2] = cm[3 * NT + c]; P2 = cm[11 * NT + c]; }
+            if (sm & (1u << 3)) { fn[3] = cm[0 * NT + c]; P3 = cm[8 * NT + c]; }
+            if (sm & (1u << 4)) { fn[4] = cm[1 * NT + c]; P4 = cm[9 * NT + c]; }
+            if (sm & (1u << 5)) fn[5] = cm[6 * NT + c];
+            if (sm & (1u << 6)) fn[6] = cm[7 * NT + c];
+            if (sm & (1u << 7)) fn[7] = cm[4 * NT + c];
+            if (sm & (1u << 8)) fn[8] = cm[5 * NT + c];
+          }
         }
-        gn[1] = pS0 + P1;
-        gn[2] = pS1 + P2;
-        gn[3] = pS2 + P3;
-        gn[4] = pS3 + P4;
-        const size_t cc = (size_t)Y * nx + x;
+        float* fo = fout + Y * nx + x;
+        float* go = gout + Y * nx + x;
 #pragma unroll
-        for (int i = 0; i < 9; i++) fout[i * N + cc] = fn[i];
-#pragma unroll
-        for (int i = 0; i < 5; i++) gout[i * N + cc] = gn[i];
+        for (int i = 0; i < 9; i++) fo[i * N] = fn[i];
+        go[0] = pG0;
+        go[N] = pS0 + P1;
+        go[2 * N] = pS1 + P2;
+        go[3 * N] = pS2 + P3;
+        go[4 * N] = pS3 + P4;
       }
+      // rotate the ring slots: the slot of R-2 becomes the slot of R+1
+      const int sn = s2;
+      s2 = s1;
+      s1 = s0;
+      s0 = sn;
+      rs0 = rs0 + 1 == D ? 0 : rs0 + 1;
+      const int rn = r3;
+      r3 = r2;
+      r2 = r1;
+      r1 = r0;
+      r0 = rn;
     }
+    cp_async_wait<0>();  // no copy may land after the block moves on
     if (DIAG) {
       // lattice sums of this item, one atomic per warp (every lane of the
       // block takes part; the block size is a multiple of 32)
@@ -443,6 +579,19 @@ __global__ void __launch_bounds__(256) step_kernel(const Inst* __restrict__ inst
     __syncthreads();
   }
 }
+
+#undef phis2
+#undef inv_phis
+#undef A4
+#undef kappa
+#undef qf
+#undef omq
+#undef inv_tphi
+#undef gamma
+#undef inv2q
+#undef nu_air
+#undef dnu
+#undef n0
 
 // ---------------------------------------------------------------------------
 // Initialisation (FP64): phi_0 of the chosen profile into a temporary.
@@ -659,10 +808,11 @@ __global__ void f_convert_kernel(const Inst* __restrict__ insts, int index, cons
 }  // namespace
 
 // ---------------------------------------------------------------------------
-size_t step_smem_bytes(int nt) {
-  size_t floats = 3 * (size_t)(nt + 4) + 3 * (size_t)(nt + 2) + 36 * (size_t)nt;
-  floats += floats & 1;
-  return floats * sizeof(float) + (size_t)((nt + 31) / 32) * 3 * sizeof(double);
+size_t step_smem_bytes(int nt, int prefetch) {
+  // nt is a multiple of 32, so the float part keeps the doubles 8-byte aligned
+  size_t ring = (size_t)(prefetch + 3) * (5 * (size_t)(nt + 4) + 9 * (size_t)nt);
+  size_t floats = ring + 4 * (size_t)(nt + 4) + 3 * (size_t)(nt + 2) + 36 * (size_t)nt;
+  return floats * sizeof(float) + (size_t)(nt / 32) * 3 * sizeof(double);
 }
 
 cudaError_t launch_init(const Inst* d_inst, const Inst& h, int index, cudaStream_t s) {
@@ -677,12 +827,20 @@ cudaError_t launch_init(const Inst* d_inst, const Inst& h, int index, cudaStream
 }
 
 cudaError_t launch_step(const Inst* d_inst, const Item* d_items, int n_items, int nthreads,
-                        int grid, const long long* d_t, int t_off, bool diag, cudaStream_t s) {
-  const size_t smem = step_smem_bytes(nthreads);
-  if (diag)
-    step_kernel<true><<<grid, nthreads, smem, s>>>(d_inst, d_items, n_items, d_t, t_off);
-  else
-    step_kernel<false><<<grid, nthreads, smem, s>>>(d_inst, d_items, n_items, d_t, t_off);
+                        int grid, const long long* d_t, int t_off, bool diag, int prefetch,
+                        cudaStream_t s) {
+  const size_t smem = step_smem_bytes(nthreads, prefetch);
+  if (prefetch == 1) {
+    if (diag)
+      step_kernel<true, 1><<<grid, nthreads, smem, s>>>(d_inst, d_items, n_items, d_t, t_off);
+    else
+      step_kernel<false, 1><<<grid, nthreads, smem, s>>>(d_inst, d_items, n_items, d_t, t_off);
+  } else {
+    if (diag)
+      step_kernel<true, 2><<<grid, nthreads, smem, s>>>(d_inst, d_items, n_items, d_t, t_off);
+    else
+      step_kernel<false, 2><<<grid, nthreads, smem, s>>>(d_inst, d_items, n_items, d_t, t_off);
+  }
   return cudaGetLastError();
 }
 
@@ -717,12 +875,20 @@ cudaError_t launch_f_import(const Inst* d_inst, const Inst& h, int index, const 
   return cudaGetLastError();
 }
 
+int step_prefetch_for(int nthreads) {
+  return 2 * step_smem_bytes(nthreads, 2) <= 227 * 1024 ? 2 : 1;
+}
+
 cudaError_t set_step_smem_limit() {
-  cudaError_t e = cudaFuncSetAttribute(step_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)step_smem_bytes(kMaxThreads));
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(step_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)step_smem_bytes(kMaxThreads));
+  const int lim = (int)step_smem_bytes(256, 2);
+  cudaError_t e = cudaFuncSetAttribute(step_kernel<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(step_kernel<false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(step_kernel<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(step_kernel<false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  return e;
 }
 
 }  // namespace ij

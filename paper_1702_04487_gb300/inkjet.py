@@ -77,6 +77,9 @@ _sig = {
     "ij_launch_count": [_vp, C.POINTER(_ll)],
     "ij_kernel_timing": [_vp, _i, _dp, C.POINTER(_ll)],
     "ij_step_noalloc": [C.POINTER(ij_params), _ll, _fp, _fp, _fp, _fp, _fp, _vp],
+    "ij_tune": [_vp, _i, _i, _i],
+    "ij_autotune": [_vp, _i],
+    "ij_get_tuning": [_vp, _i, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i), C.POINTER(_i)],
     "ij_destroy": [_vp],
 }
 for _name, _args in _sig.items():
@@ -230,6 +233,25 @@ def ij_kernel_timing(h, enable=-1):
     ms, n = C.c_double(), C.c_longlong()
     _check(_lib.ij_kernel_timing(h.ptr, int(enable), C.byref(ms), C.byref(n)))
     return ms.value, n.value
+
+
+def ij_tune(h, block_size=0, chunk=32, prefetch=2):
+    _check(_lib.ij_tune(h.ptr, int(block_size), int(chunk), int(prefetch)))
+
+
+def ij_autotune(h, reps=3):
+    _check(_lib.ij_autotune(h.ptr, int(reps)))
+    return ij_get_tuning(h)
+
+
+def ij_get_tuning(h):
+    """List of dicts (block_size, chunk, prefetch, items), one per bucket."""
+    out, k = [], 0
+    vals = [C.c_int() for _ in range(4)]
+    while _lib.ij_get_tuning(h.ptr, k, *[C.byref(v) for v in vals]) == IJ_OK:
+        out.append(dict(zip(("block_size", "chunk", "prefetch", "items"), [v.value for v in vals])))
+        k += 1
+    return out
 
 
 def ij_destroy(h):

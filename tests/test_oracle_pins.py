@@ -371,3 +371,26 @@ def test_breakup_rule_agrees_with_connected_components():
     assert _components(s2.fields()["phi"] > 0) == 1
     s2.step(100 + 40)
     assert _components(s2.fields()["phi"] > 0) >= 2
+
+
+@pytest.mark.slow
+def test_fp32_noise_floor_of_cfg1():
+    """The round-off floor that bounds any FP32 implementation of cfg 1: two
+    oracle runs that each take a relative 2^-24 (FP32 rounding) perturbation
+    of every population after every step end up, after 1000 steps, a few
+    1e-6 to ~1.5e-5 of phi* from the exact run, concentrated at the driven
+    meniscus.  The GPU parity bound on phi (3e-5) stays at about twice this
+    floor."""
+    p = W.cfg1("spec")
+    ref = OracleSim(p)
+    noisy = OracleSim(p)
+    rng = np.random.default_rng(12)
+    eps = 2.0 ** -24
+    for t in range(1, 1001):
+        ref.step(1)
+        noisy.step(1)
+        f, g = noisy.state()
+        noisy.set_state(f * (1 + eps * rng.uniform(-1, 1, f.shape)),
+                        g * (1 + eps * rng.uniform(-1, 1, g.shape)), t)
+    d = np.abs(noisy.state()[1].sum(0) - ref.state()[1].sum(0)).max() / 4.5
+    assert 2e-6 < d < 1.5e-5
