@@ -194,6 +194,11 @@ ij_status ij_kernel_timing(ij_handle h, int enable, double* total_ms, long long*
  *                 `bucket` (0-based); IJ_ERR_PARAM past the last bucket.
  */
 ij_status ij_tune(ij_handle h, int block_size, int chunk, int prefetch);
+/* ij_use_graph -- run whole diagnostics periods (diag_every steps, or 16
+ * when diagnostics are off) of ij_step as one replay of a captured CUDA
+ * graph (enable = 1, the default) or as separate launches (0).  Both give
+ * identical results; the graph removes per-launch overhead. */
+ij_status ij_use_graph(ij_handle h, int enable);
 ij_status ij_autotune(ij_handle h, int reps);
 ij_status ij_get_tuning(ij_handle h, int bucket, int* block_size, int* chunk, int* prefetch,
                         int* items);

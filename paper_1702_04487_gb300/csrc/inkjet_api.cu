@@ -84,6 +84,16 @@ struct ij_handle_s {
   ij_free_fn free_fn = nullptr;
   void* ctx = nullptr;
   std::vector<void*> blocks;
+  // CUDA graph of one diagnostics period (diag_every steps, or 16)
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int graph_steps = 0;
+  long long graph_launches = 0;  // kernels per graph launch
+  bool use_graph = true;
+  void drop_graph() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    gexec = nullptr;
+  }
   // optional CUDA-event timing of the step-kernel launches
   bool timing = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
@@ -120,6 +130,9 @@ struct ij_handle_s {
   void release() {
     if (stream) cudaStreamSynchronize(stream); else cudaDeviceSynchronize();
     drain_events();
+    drop_graph();
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+    cap_stream = nullptr;
     for (void* p : blocks) {
       if (free_fn) free_fn(p, ctx); else cudaFree(p);
     }
@@ -264,8 +277,10 @@ void build_items(ij_handle h) {
   }
 }
 
-// Upload the work list, growing the device copy when needed.
+// Upload the work list, growing the device copy when needed (the captured
+// graph bakes the list in, so it is rebuilt on the next ij_step).
 ij_status upload_items(ij_handle h) {
+  h->drop_graph();
   if (h->items.size() > h->items_cap) {
     Item* p = (Item*)h->dalloc(h->items.size() * sizeof(Item));
     if (!p) return fail(IJ_ERR_OOM, "device allocation of the work list failed");
@@ -308,6 +323,48 @@ ij_status one_step(ij_handle h) {
   CUDA_TRY(launch_advance(h->d_t, 1, h->stream));
   h->launches++;
   h->t++;
+  return IJ_OK;
+}
+
+// Capture one diagnostics period into a graph: the step kernels of every
+// bucket with time offsets 0..P-1 (offset 0 with diagnostics when enabled),
+// the record kernel after the first step, and one advance of the time by P.
+ij_status build_graph(ij_handle h) {
+  h->drop_graph();
+  const int P = h->diag_every > 0 ? h->diag_every : 16;
+  if (!h->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  cudaStream_t cs = h->cap_stream;
+  CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  long long n = 0;
+  cudaError_t e = cudaSuccess;
+  for (int j = 0; j < P && e == cudaSuccess; j++) {
+    const bool diag = h->diag_every > 0 && j == 0;
+    for (const Bucket& b : h->buckets) {
+      e = launch_step(h->d_inst, h->d_items + b.first, b.count, b.nthreads, b.grid, h->d_t, j,
+                      diag, b.prefetch, cs);
+      n++;
+      if (e != cudaSuccess) break;
+    }
+    if (diag && e == cudaSuccess) {
+      e = launch_finalize(h->d_inst, h->n_inst, h->d_t, cs);
+      n++;
+    }
+  }
+  if (e == cudaSuccess) {
+    e = launch_advance(h->d_t, P, cs);
+    n++;
+  }
+  cudaGraph_t g = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return fail(IJ_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+  }
+  e = cudaGraphInstantiate(&h->gexec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(IJ_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  h->graph_steps = P;
+  h->graph_launches = n;
   return IJ_OK;
 }
 
@@ -420,9 +477,25 @@ ij_status ij_step(ij_handle h, long long nsteps) {
   }
   if (h->poisoned)
     return fail(IJ_ERR_NUMERIC, "every lattice of the handle has produced NaN or |u| > 0.3");
-  for (long long k = 0; k < nsteps; k++) {
-    st = one_step(h);
-    if (st != IJ_OK) return st;
+  long long left = nsteps;
+  while (left > 0) {
+    const int P = h->diag_every > 0 ? h->diag_every : 16;
+    // whole diagnostics periods run as one graph launch (not while the
+    // step kernels are being timed launch by launch)
+    if (h->use_graph && !h->timing && left >= P && h->t % P == 0) {
+      if (!h->gexec) {
+        st = build_graph(h);
+        if (st != IJ_OK) return st;
+      }
+      CUDA_TRY(cudaGraphLaunch(h->gexec, h->stream));
+      h->launches += h->graph_launches;
+      h->t += P;
+      left -= P;
+    } else {
+      st = one_step(h);
+      if (st != IJ_OK) return st;
+      left--;
+    }
   }
   CUDA_TRY(cudaMemcpyAsync(h->h_status, h->d_status, h->n_inst * sizeof(unsigned),
                            cudaMemcpyDeviceToHost, h->stream));
@@ -648,6 +721,13 @@ ij_status ij_autotune(ij_handle h, int reps) {
   cudaEventDestroy(e1);
   build_items(h);
   return upload_items(h);
+}
+
+ij_status ij_use_graph(ij_handle h, int enable) {
+  ij_status st = check_handle(h);
+  if (st != IJ_OK) return st;
+  h->use_graph = enable != 0;
+  return IJ_OK;
 }
 
 ij_status ij_get_tuning(ij_handle h, int bucket, int* block_size, int* chunk, int* prefetch,

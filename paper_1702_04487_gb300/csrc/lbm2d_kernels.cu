@@ -705,22 +705,99 @@ __global__ void zero_kernel(float* a, size_t n) {
 }
 
 // ---------------------------------------------------------------------------
-// Diagnostics record (FP64), one block per lattice, one thread does the
-// row scans; the row accumulators are cleared for the next record.
-__global__ void finalize_kernel(const Inst* __restrict__ insts, const long long* d_t) {
+// Diagnostics record (FP64), one block of kFinThreads per lattice.  Each thread
+// owns a contiguous range of rows; suffix sums, minima and run boundaries are
+// combined across threads through shared memory.  The row accumulators are
+// cleared for the next record.
+constexpr int kFinThreads = 256;
+
+__device__ double block_sum(double v, double* sh) {
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = kFinThreads / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  const double r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+__device__ double block_min(double v, double* sh) {
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = kFinThreads / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sh[threadIdx.x] = fmin(sh[threadIdx.x], sh[threadIdx.x + o]);
+    __syncthreads();
+  }
+  const double r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(kFinThreads) finalize_kernel(const Inst* __restrict__ insts,
+                                                              const long long* d_t) {
+  __shared__ double sh[kFinThreads];
+  __shared__ double suffix[kFinThreads + 1];
   const Inst& I = insts[blockIdx.x];
-  const int ny = I.ny;
-  double* w = I.rows;
-  double* m = I.rows + ny;
-  double* pr = I.rows + 2 * ny;
-  if (threadIdx.x == 0) {
+  const int ny = I.ny, tid = threadIdx.x;
+  const double* w = I.rows;
+  const double* m = I.rows + ny;
+  const double* pr = I.rows + 2 * ny;
+  const int per = (ny + kFinThreads - 1) / kFinThreads;
+  const int ya = min(ny, tid * per), yb = min(ny, ya + per);
+  // run ink of this thread's rows, then the run ink strictly above each thread
+  double mine = 0.0;
+  for (int y = ya; y < yb; y++)
+    if (w[y] > 0.5) mine += w[y];
+  sh[tid] = mine;
+  __syncthreads();
+  if (tid == 0) {
+    suffix[kFinThreads] = 0.0;
+    for (int k = kFinThreads - 1; k >= 0; k--) suffix[k] = suffix[k + 1] + sh[k];
+  }
+  __syncthreads();
+  // neck: least w(y) over rows y >= y_scan with more than vmin of run ink above
+  double above = suffix[tid + 1], neck = 1e30;
+  for (int y = yb - 1; y >= ya; y--) {
+    if (y >= I.y_scan && above > I.vmin && w[y] < neck) neck = w[y];
+    if (w[y] > 0.5) above += w[y];
+  }
+  neck = block_min(neck, sh);
+  // runs of rows with w > 1/2
+  double starts = 0.0, starts_above = 0.0, last_start = -1.0;
+  for (int y = ya; y < yb; y++)
+    if (w[y] > 0.5 && (y == 0 || w[y - 1] <= 0.5)) {
+      starts += 1.0;
+      if (y >= I.y_exit) starts_above += 1.0;
+      last_start = y;
+    }
+  const double nruns = block_sum(starts, sh);
+  const double nabove = block_sum(starts_above, sh);
+  const int lead0 = (int)(-block_min(-last_start, sh));
+  double end = ny;
+  if (lead0 >= 0)
+    for (int y = max(ya, lead0 + 1); y < yb; y++)
+      if (!(w[y] > 0.5)) {
+        end = y;
+        break;
+      }
+  const int lead1 = (int)block_min(end, sh);
+  double vol = 0, ycm = 0, mm = 0, pp = 0;
+  if (lead0 >= 0)
+    for (int y = max(ya, lead0); y < min(yb, lead1); y++) {
+      vol += w[y];
+      ycm += y * w[y];
+      mm += m[y];
+      pp += pr[y];
+    }
+  vol = block_sum(vol, sh);
+  ycm = block_sum(ycm, sh);
+  mm = block_sum(mm, sh);
+  pp = block_sum(pp, sh);
+  if (tid == 0) {
     const double t = (double)*d_t;
     double* st = I.dstate;
-    double neck = 1e30, above = 0.0;
-    for (int y = ny - 1; y >= 0; y--) {
-      if (y >= I.y_scan && above > I.vmin && w[y] < neck) neck = w[y];
-      if (w[y] > 0.5) above += w[y];
-    }
     const double thr = 0.01;  // neck width at pinch-off, cells of ink
     if (st[3] < 0.0 && neck < thr) {
       if (st[0] > 0.0 && st[1] >= thr && st[1] < 1e29)
@@ -731,26 +808,6 @@ __global__ void finalize_kernel(const Inst* __restrict__ insts, const long long*
     st[0] = 1.0;
     st[1] = neck;
     st[2] = t;
-    int nruns = 0, nabove = 0, lead0 = -1, lead1 = -1;
-    for (int y = 0; y < ny;) {
-      if (w[y] > 0.5) {
-        int ya = y;
-        while (y < ny && w[y] > 0.5) y++;
-        nruns++;
-        if (ya >= I.y_exit) nabove++;
-        lead0 = ya;
-        lead1 = y;
-      } else {
-        y++;
-      }
-    }
-    double vol = 0, ycm = 0, mm = 0, pp = 0;
-    for (int y = lead0; lead0 >= 0 && y < lead1; y++) {
-      vol += w[y];
-      ycm += y * w[y];
-      mm += m[y];
-      pp += pr[y];
-    }
     const long long cnt = (long long)st[4];
     double* rec = I.hist + (cnt % kHistCap) * kRec;
     rec[0] = t;
@@ -769,7 +826,7 @@ __global__ void finalize_kernel(const Inst* __restrict__ insts, const long long*
     I.sums[0] = I.sums[1] = I.sums[2] = I.sums[3] = 0.0;
   }
   __syncthreads();
-  for (int y = threadIdx.x; y < 3 * ny; y += blockDim.x) I.rows[y] = 0.0;
+  for (int y = tid; y < 3 * ny; y += kFinThreads) I.rows[y] = 0.0;
 }
 
 __global__ void advance_kernel(long long* d_t, int by) { *d_t += by; }
@@ -845,7 +902,7 @@ cudaError_t launch_step(const Inst* d_inst, const Item* d_items, int n_items, in
 }
 
 cudaError_t launch_finalize(const Inst* d_inst, int n_inst, const long long* d_t, cudaStream_t s) {
-  finalize_kernel<<<n_inst, 256, 0, s>>>(d_inst, d_t);
+  finalize_kernel<<<n_inst, kFinThreads, 0, s>>>(d_inst, d_t);
   return cudaGetLastError();
 }
 

@@ -79,6 +79,7 @@ _sig = {
     "ij_step_noalloc": [C.POINTER(ij_params), _ll, _fp, _fp, _fp, _fp, _fp, _vp],
     "ij_tune": [_vp, _i, _i, _i],
     "ij_autotune": [_vp, _i],
+    "ij_use_graph": [_vp, _i],
     "ij_get_tuning": [_vp, _i, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i), C.POINTER(_i)],
     "ij_destroy": [_vp],
 }
@@ -237,6 +238,10 @@ def ij_kernel_timing(h, enable=-1):
 
 def ij_tune(h, block_size=0, chunk=32, prefetch=2):
     _check(_lib.ij_tune(h.ptr, int(block_size), int(chunk), int(prefetch)))
+
+
+def ij_use_graph(h, enable=True):
+    _check(_lib.ij_use_graph(h.ptr, int(bool(enable))))
 
 
 def ij_autotune(h, reps=3):

@@ -234,3 +234,32 @@ def test_zero_steps_and_bad_index(ij):
         ij.ij_get_state(h, 3)
     with pytest.raises(ij.InkjetError):
         ij.ij_step(h, -1)
+
+
+def test_graph_replay_tuning_and_autotune_leave_results_bitwise_equal(ij):
+    """The same batch advanced by direct launches, by CUDA-graph replay, with
+    another row chunk and prefetch, and after an autotune (whose trial
+    launches must leave the state and the time untouched) gives bitwise
+    identical populations and diagnostics."""
+    ps = W.cfg3_sample(count=4, seed=21)
+    ps = [dict(q, ny=min(q["ny"], 300)) for q in ps]
+    ref = ij.ij_create(ps)
+    ij.ij_use_graph(ref, False)
+    ij.ij_step(ref, 37)
+    other = ij.ij_create(ps)
+    ij.ij_autotune(other, 1)
+    assert ij.ij_time(other) == 0
+    f0, g0 = ij.ij_get_state(other, 0)
+    f0r, g0r = ij.ij_get_state(ij.ij_create(ps), 0)
+    assert np.array_equal(f0, f0r) and np.array_equal(g0, g0r)
+    ij.ij_step(other, 20)        # graph replay (two periods of 10)
+    ij.ij_tune(other, 0, 24, 1)  # another launch shape mid-run
+    ij.ij_step(other, 17)
+    assert ij.ij_time(other) == 37
+    for k in range(len(ps)):
+        fa, ga = ij.ij_get_state(ref, k)
+        fb, gb = ij.ij_get_state(other, k)
+        assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
+        ha, hb = ij.ij_history(ref, k), ij.ij_history(other, k)
+        assert ha.shape == hb.shape
+        assert np.allclose(ha, hb, rtol=1e-12, atol=1e-12)
