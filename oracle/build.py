@@ -7,7 +7,7 @@ import os
 import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SRC = os.path.join(HERE, "lbm_oracle.c")
+SRCS = [os.path.join(HERE, "lbm_oracle.c"), os.path.join(HERE, "lbm3d_oracle.c")]
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liboracle.so")
 
@@ -15,7 +15,7 @@ LIB = os.path.join(OUT_DIR, "liboracle.so")
 def build(force: bool = False) -> str:
     """Compile the oracle if the shared library is missing or stale."""
     os.makedirs(OUT_DIR, exist_ok=True)
-    deps = [SRC, os.path.join(HERE, "lbm_oracle.h")]
+    deps = SRCS + [os.path.join(HERE, "lbm_oracle.h")]
     if (not force and os.path.exists(LIB)
             and os.path.getmtime(LIB) >= max(os.path.getmtime(d) for d in deps)):
         return LIB
@@ -23,7 +23,7 @@ def build(force: bool = False) -> str:
     # -ffp-contract=off: no fused multiply-adds, so the FP64 arithmetic is the
     # plain sequence of operations written in the source on every host.
     cmd = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-ffp-contract=off",
-           "-fPIC", "-shared", SRC, "-o", tmp, "-lm"]
+           "-fPIC", "-shared"] + SRCS + ["-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, LIB)
     return LIB

@@ -54,6 +54,8 @@ typedef struct {
   double jitter;
   unsigned long long seed;
   int diag_every;
+  int nz;        /* 3-D only: lattice depth along the nozzle axis z */
+  double init_z; /* 3-D only: drop centre z */
 } orc_params;
 
 typedef struct orc_sim orc_sim;
@@ -77,6 +79,23 @@ int orc_history(const orc_sim* s, double* out, int max_records);
 void orc_kinds(const orc_sim* s, unsigned char* out);
 /* Streaming with boundary rules alone (identity collision, q = 1). */
 void orc_stream_only(orc_sim* s, const double* fin, const double* gin, double* fout, double* gout);
+
+/* 3-D lift (lbm3d_oracle.c): D3Q19 / D3Q7, z the nozzle axis; the nozzle
+ * radius is nozzle_width.  Same conventions as the 2-D calls above. */
+void* orc3_create(const orc_params* p);
+void orc3_destroy(void* s);
+void orc3_step(void* s, long long nsteps);
+long long orc3_time(const void* s);
+void orc3_get_state(const void* s, double* f, double* g);
+void orc3_set_state(void* s, const double* f, const double* g, long long t);
+void orc3_kinds(const void* s, unsigned char* out);
+int orc3_history(const void* s, double* out, int max_records);
+void orc3_stream_only(void* s, const double* fin, const double* gin, double* fout, double* gout);
+void orc3_feq(double n, double phi, double mu, const double* u, double* feq19);
+void orc3_geq(double phi, double mu, const double* u, double gamma, double q, double* geq7);
+void orc3_force_term(double tau, const double* u, const double* F, double* F19);
+void orc3_lattice(int* ex, int* ey, int* ez, double* w);
+double orc3_uniform(unsigned long long seed, int x, int y, int z);
 
 /* Per-cell building blocks, exposed for the closed-form tests. */
 void orc_feq(double n, double phi, double mu, double ux, double uy, double* feq9);

@@ -31,6 +31,8 @@ class _Params(C.Structure):
         ("jitter", C.c_double),
         ("seed", C.c_ulonglong),
         ("diag_every", C.c_int),
+        ("nz", C.c_int),
+        ("init_z", C.c_double),
     ]
 
 
@@ -38,7 +40,7 @@ DEFAULTS = dict(nx=8, ny=8, geometry=0, nozzle_width=0, nozzle_length=0, wall_th
                 rho_ink=10.0, rho_air=1.0, nu_ink=0.1, nu_air=0.05, sigma=0.01, width_W=3.0,
                 tau_phi=0.8, gamma=0.0, theta_deg=90.0, F0=0.0, F_neg=0.0, T1=0, T2=0,
                 T_idle=0, axial_bc=0, init_kind=0, init_x=0.0, init_y=0.0, init_r=0.0,
-                jitter=1e-6, seed=0, diag_every=0)
+                jitter=1e-6, seed=0, diag_every=0, nz=1, init_z=0.0)
 
 _lib = None
 
@@ -177,3 +179,111 @@ def omega_of_theta(theta_deg):
 
 def uniform(seed, x, y):
     return _load().orc_uniform(seed, x, y)
+
+
+def _load3():
+    lib = _load()
+    if not getattr(lib, "_orc3_ready", False):
+        dp = C.POINTER(C.c_double)
+        lib.orc3_create.restype = C.c_void_p
+        lib.orc3_create.argtypes = [C.POINTER(_Params)]
+        lib.orc3_destroy.argtypes = [C.c_void_p]
+        lib.orc3_step.argtypes = [C.c_void_p, C.c_longlong]
+        lib.orc3_time.restype = C.c_longlong
+        lib.orc3_time.argtypes = [C.c_void_p]
+        lib.orc3_get_state.argtypes = [C.c_void_p, dp, dp]
+        lib.orc3_set_state.argtypes = [C.c_void_p, dp, dp, C.c_longlong]
+        lib.orc3_kinds.argtypes = [C.c_void_p, C.POINTER(C.c_ubyte)]
+        lib.orc3_history.restype = C.c_int
+        lib.orc3_history.argtypes = [C.c_void_p, dp, C.c_int]
+        lib.orc3_stream_only.argtypes = [C.c_void_p, dp, dp, dp, dp]
+        lib.orc3_feq.argtypes = [C.c_double] * 3 + [dp, dp]
+        lib.orc3_geq.argtypes = [C.c_double, C.c_double, dp, C.c_double, C.c_double, dp]
+        lib.orc3_force_term.argtypes = [C.c_double, dp, dp, dp]
+        lib.orc3_lattice.argtypes = [C.POINTER(C.c_int)] * 3 + [dp]
+        lib.orc3_uniform.restype = C.c_double
+        lib.orc3_uniform.argtypes = [C.c_ulonglong, C.c_int, C.c_int, C.c_int]
+        lib._orc3_ready = True
+    return lib
+
+
+class OracleSim3:
+    """One FP64 3-D lattice (D3Q19/D3Q7); arrays are (19|7, nz, ny, nx)."""
+
+    def __init__(self, params: dict):
+        self.lib = _load3()
+        self.params = dict(DEFAULTS, **params)
+        self._p = make_params(params)
+        self.nx, self.ny, self.nz = self._p.nx, self._p.ny, self._p.nz
+        self.h = self.lib.orc3_create(C.byref(self._p))
+        if not self.h:
+            raise ValueError("oracle rejected parameters")
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            self.lib.orc3_destroy(h)
+            self.h = None
+
+    def step(self, n=1):
+        self.lib.orc3_step(self.h, int(n))
+
+    @property
+    def t(self):
+        return self.lib.orc3_time(self.h)
+
+    def state(self):
+        f = np.empty((19, self.nz, self.ny, self.nx))
+        g = np.empty((7, self.nz, self.ny, self.nx))
+        self.lib.orc3_get_state(self.h, _dp(f), _dp(g))
+        return f, g
+
+    def set_state(self, f, g, t=0):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        g = np.ascontiguousarray(g, dtype=np.float64)
+        self.lib.orc3_set_state(self.h, _dp(f), _dp(g), int(t))
+
+    def kinds(self):
+        out = np.empty((self.nz, self.ny, self.nx), dtype=np.uint8)
+        self.lib.orc3_kinds(self.h, out.ctypes.data_as(C.POINTER(C.c_ubyte)))
+        return out
+
+    def history(self):
+        n = self.lib.orc3_history(self.h, None, 0)
+        out = np.empty((max(n, 1), len(REC_FIELDS)))
+        self.lib.orc3_history(self.h, _dp(out), n)
+        return out[:n]
+
+    def stream_only(self, f, g):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        g = np.ascontiguousarray(g, dtype=np.float64)
+        fo, go = np.empty_like(f), np.empty_like(g)
+        self.lib.orc3_stream_only(self.h, _dp(f), _dp(g), _dp(fo), _dp(go))
+        return fo, go
+
+
+def lattice3():
+    lib = _load3()
+    ex, ey, ez = (C.c_int * 19)(), (C.c_int * 19)(), (C.c_int * 19)()
+    w = np.empty(19)
+    lib.orc3_lattice(ex, ey, ez, _dp(w))
+    return np.array(ex[:]), np.array(ey[:]), np.array(ez[:]), w
+
+
+def feq3(n, phi, mu, u):
+    out = np.empty(19)
+    _load3().orc3_feq(n, phi, mu, _dp(np.ascontiguousarray(u, dtype=np.float64)), _dp(out))
+    return out
+
+
+def geq3(phi, mu, u, gamma, q):
+    out = np.empty(7)
+    _load3().orc3_geq(phi, mu, _dp(np.ascontiguousarray(u, dtype=np.float64)), gamma, q, _dp(out))
+    return out
+
+
+def force_term3(tau, u, F):
+    out = np.empty(19)
+    _load3().orc3_force_term(tau, _dp(np.ascontiguousarray(u, dtype=np.float64)),
+                             _dp(np.ascontiguousarray(F, dtype=np.float64)), _dp(out))
+    return out

@@ -1,0 +1,123 @@
+"""Pins of the 3-D (D3Q19/D3Q7) oracle against closed forms and invariants.
+
+The paper is 2-D; its 3-D lift matches the moments of Eq. 5-6 and 9-10 on
+the D3Q19/D3Q7 lattices.  These tests fix the lattice tables, the
+equilibria, the forcing term, the streaming and the conservation laws.
+"""
+import numpy as np
+import pytest
+
+from oracle import OracleSim3, feq3, force_term3, geq3, lattice3
+from paper_1702_04487_gb300 import workloads as W
+
+EX, EY, EZ, WT = lattice3()
+C = np.stack([EX, EY, EZ], axis=1).astype(float)
+OPP = np.array([int(np.where((C == -C[i]).all(1))[0][0]) for i in range(19)])
+
+
+def test_d3q19_table_isotropy():
+    """Weights sum to one; second moment 1/3 I; fourth moment isotropic
+    (1/9 for xxyy, 1/3 for xxxx), the conditions that make the lift recover
+    the same continuum equations as D2Q9."""
+    assert abs(WT.sum() - 1) < 1e-15
+    M2 = np.einsum("i,ia,ib->ab", WT, C, C)
+    assert np.allclose(M2, np.eye(3) / 3, atol=1e-15)
+    M4 = np.einsum("i,ia,ib,ic,id->abcd", WT, C, C, C, C)
+    assert abs(M4[0, 0, 1, 1] - 1 / 9) < 1e-15 and abs(M4[0, 0, 0, 0] - 1 / 3) < 1e-15
+    assert abs(M4[0, 0, 0, 1]) < 1e-15
+    assert np.array_equal(C[:7][1:].sum(0), np.zeros(3))  # D3Q7 = rest + 6 axis directions
+
+
+def test_feq3_moments():
+    rng = np.random.default_rng(2)
+    for _ in range(20):
+        n, phi, mu = rng.uniform(1, 10), rng.uniform(-5, 5), rng.uniform(-1e-2, 1e-2)
+        u = rng.uniform(-0.1, 0.1, 3)
+        f = feq3(n, phi, mu, u)
+        p = n / 3 + phi * mu
+        assert abs(f.sum() - n) < 1e-13 * n
+        assert np.allclose(f @ C, n * u, atol=1e-13 * n)
+        assert np.allclose(np.einsum("i,ia,ib->ab", f, C, C), p * np.eye(3) + n * np.outer(u, u),
+                           atol=1e-13 * n)
+
+
+def test_force3_guo_moments():
+    rng = np.random.default_rng(4)
+    for _ in range(20):
+        tau = rng.uniform(0.55, 2.0)
+        u, F = rng.uniform(-0.1, 0.1, 3), rng.uniform(-1e-3, 1e-3, 3)
+        Fi = force_term3(tau, u, F)
+        a = 1 - 1 / (2 * tau)
+        assert abs(Fi.sum()) < 1e-16
+        assert np.allclose(Fi @ C, a * F, atol=1e-16)
+        assert np.allclose(np.einsum("i,ia,ib->ab", Fi, C, C), a * (np.outer(u, F) + np.outer(F, u)),
+                           atol=1e-16)
+
+
+def test_geq3_moments():
+    rng = np.random.default_rng(6)
+    C7 = C[:7]
+    for _ in range(20):
+        phi, mu = rng.uniform(-5, 5), rng.uniform(-1e-2, 1e-2)
+        u = rng.uniform(-0.1, 0.1, 3)
+        gamma, q = 5.1, 1 / 1.3
+        g = geq3(phi, mu, u, gamma, q)
+        assert abs(g.sum() - phi) < 1e-13
+        assert np.allclose(g @ C7, phi * u / q, atol=1e-13)
+        assert np.allclose(np.einsum("i,ia,ib->ab", g, C7, C7), gamma * mu * np.eye(3), atol=1e-13)
+
+
+def _nozzle3(**kw):
+    p = dict(nx=18, ny=18, nz=24, geometry=W.GEOM_NOZZLE, nozzle_width=4, nozzle_length=10,
+             wall_thickness=2, rho_ink=10.0, rho_air=1.0, nu_ink=0.1, nu_air=0.05, sigma=0.01,
+             width_W=3.0, tau_phi=0.8, theta_deg=60.0, F0=2e-3, F_neg=1e-3, T1=60, T2=60,
+             axial_bc=W.BC_CLOSED, init_kind=W.INIT_MENISCUS, jitter=1e-6, seed=3, diag_every=1)
+    p.update(kw)
+    return p
+
+
+@pytest.mark.parametrize("bc", [W.BC_PERIODIC, W.BC_CLOSED])
+def test_streaming3_is_an_exact_permutation(bc):
+    s = OracleSim3(_nozzle3(axial_bc=bc))
+    fluid = s.kinds() == 0
+    shape = (s.nz, s.ny, s.nx)
+    f = np.arange(19 * np.prod(shape), dtype=float).reshape((19,) + shape) + 1
+    g = np.arange(7 * np.prod(shape), dtype=float).reshape((7,) + shape) + 1e7
+    fo, go = s.stream_only(f, g)
+    assert np.array_equal(np.sort(fo[:, fluid].ravel()), np.sort(f[:, fluid].ravel()))
+    assert np.array_equal(np.sort(go[:, fluid].ravel()), np.sort(g[:, fluid].ravel()))
+    fr, gr = s.stream_only(fo[OPP], go[OPP[:7]])
+    assert np.array_equal(fr[OPP][:, fluid], f[:, fluid])
+    assert np.array_equal(gr[OPP[:7]][:, fluid], g[:, fluid])
+
+
+@pytest.mark.parametrize("bc", [W.BC_PERIODIC, W.BC_CLOSED])
+def test_mass3_conserved(bc):
+    s = OracleSim3(_nozzle3(axial_bc=bc))
+    s.step(150)
+    h = s.history()
+    assert np.abs(h[:, 1] - h[0, 1]).max() < 1e-12 * h[0, 1]
+    assert np.abs(h[:, 2] - h[0, 2]).max() < 1e-12 * 4.5 * 18 * 18 * 24
+    assert np.abs(h[:, 3]).max() > 1e-3
+
+
+def test_momentum3_budget_uniform_box():
+    p = _nozzle3(nx=5, ny=4, nz=6, geometry=W.GEOM_NONE, axial_bc=W.BC_PERIODIC,
+                 init_kind=W.INIT_UNIFORM, init_r=4.5, F0=1e-4, F_neg=3e-5, T1=4, T2=3)
+    s = OracleSim3(p)
+    s.step(10)
+    h = s.history()
+    F = np.array([1e-4] * 4 + [-3e-5] * 3 + [0.0] * 3)
+    N = 5 * 4 * 6
+    expect = (np.concatenate([[0.0], np.cumsum(F)[:-1]]) + F / 2) * N
+    assert np.allclose(h[:, 3], expect, rtol=1e-12, atol=1e-16)
+
+
+def test_flat_interface3_profile():
+    p = _nozzle3(nx=2, ny=2, nz=60, geometry=W.GEOM_NONE, init_kind=W.INIT_FLAT, init_y=30,
+                 F0=0.0, F_neg=0.0, jitter=0.0, nu_air=0.1, diag_every=0)
+    s = OracleSim3(p)
+    s.step(3000)
+    phi = s.state()[1].sum(0)[:, 0, 0]
+    z = np.arange(60)
+    assert np.abs(phi - 4.5 * np.tanh((30 - z) / 3.0)).max() < 0.01 * 4.5
