@@ -23,7 +23,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "MLUPS & %HBM peak, plain vs batched/FP16-store LBM; surrogate speedup at err"
-BYTES_PER_LUP = 112  # (9 + 5) FP32 populations read once and written once
+# Algorithmic bytes per lattice update: the stored populations read once and
+# written once.  2-D: (9 + 5) FP32.  3-D: (19 + 7) FP32, or with FP16
+# storage 19 + 6 FP16 and g_0 in FP32.
+BYTES_PER_LUP = {"2d": 112, "3d32": 208, "3d16": 108}
 FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes per step-kernel launch from an ncu capture (dram__bytes_read.sum
 # + dram__bytes_write.sum) of the workload below, valid only for the kernel
@@ -31,9 +34,31 @@ FALLBACK_HBM_GBS = 6800.0
 NCU_TRAFFIC = {}
 
 
-def kernel_hash():
-    with open(os.path.join(ROOT, "paper_1702_04487_gb300", "csrc", "lbm2d_kernels.cu"), "rb") as fh:
+def kernel_hash(params):
+    name = "lbm3d_kernels.cu" if params[0].get("dim", 2) == 3 else "lbm2d_kernels.cu"
+    with open(os.path.join(ROOT, "paper_1702_04487_gb300", "csrc", name), "rb") as fh:
         return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def lattice_kind(p):
+    if p.get("dim", 2) != 3:
+        return "2d"
+    return "3d16" if p.get("precision", 0) == 1 else "3d32"
+
+
+def cells_of(p):
+    return p["nx"] * p["ny"] * (p["nz"] if p.get("dim", 2) == 3 else 1)
+
+
+def device_bytes(p):
+    """Device bytes the handle holds per lattice (state, work copy, phi)."""
+    c = cells_of(p)
+    k = lattice_kind(p)
+    if k == "2d":
+        return c * 14 * 4 * 2
+    es = 2 if k == "3d16" else 4
+    planes = c // p["nz"] * (p["nz"] + 2)
+    return c * (25 * es + 8) + planes * (25 * es + 4)
 
 
 def workload(name, rank=0):
@@ -47,6 +72,11 @@ def workload(name, rank=0):
     elif name == "cfg3":
         ps = W.cfg3_sample(seed=3 + 1000 * rank)
         desc = "256 uneven nozzle lattices (w in [16,48], 4w x 30w), FP32"
+    elif name in ("cfg4", "cfg4h"):
+        prec = 1 if name == "cfg4h" else 0
+        ps = [W.cfg4(60.0, prec, seed=4 + 2 * rank), W.cfg4(120.0, prec, seed=5 + 2 * rank)]
+        desc = ("3-D round nozzle 128x128x640 (R 24, L 160), contact angles 60 and 120, "
+                "2 lattices, D3Q19/D3Q7, %s storage" % ("FP16 offset" if prec else "FP32"))
     else:
         raise SystemExit("unknown workload " + name)
     return ps, desc
@@ -118,22 +148,33 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def oracle_sample(params):
+    """The oracle and the lattice it times: lattice 0 of the workload (2-D),
+    or its 32x32x160 downscale (3-D, where one full-size step takes ~15 s)."""
+    p = params[0]
+    if p.get("dim", 2) == 3:
+        from oracle import OracleSim3
+        from paper_1702_04487_gb300 import workloads as W
+        q = W.cfg4_downscale(p["theta_deg"])
+        q = {k: v for k, v in q.items() if k not in ("dim", "precision")}
+        return OracleSim3(q), q, "%dx%dx%d downscale of lattice 0" % (q["nx"], q["ny"], q["nz"])
+    from oracle import OracleSim
+    return OracleSim(p), p, "one %dx%d lattice (lattice 0 of the workload)" % (p["nx"], p["ny"])
+
+
 def cpu_baseline(params, seconds=12.0):
     """The FP64 oracle, as it stands, on one lattice of the workload."""
-    from oracle import OracleSim
-    p = params[0]
-    sim = OracleSim(p)
-    cells = p["nx"] * p["ny"]
+    sim, p, what = oracle_sample(params)
+    cells = cells_of(dict(p, dim=params[0].get("dim", 2)))
     t0 = time.perf_counter()
-    sim.step(2)
-    per = (time.perf_counter() - t0) / 2
-    n = max(2, int(seconds / max(per, 1e-6)))
+    sim.step(1)
+    per = time.perf_counter() - t0
+    n = max(1, int(seconds / max(per, 1e-6)))
     t0 = time.perf_counter()
     sim.step(n)
     dt = time.perf_counter() - t0
     return {"value": cells * n / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": "%d steps of one %dx%d lattice (lattice 0 of the workload), FP64, "
-                      "single-threaded C" % (n, p["nx"], p["ny"])}
+            "sample": "%d steps of %s, FP64, single-threaded C" % (n, what)}
 
 
 def run_reference(args):
@@ -141,17 +182,14 @@ def run_reference(args):
     if rank != 0:
         return
     params, desc = workload(args.workload)
-    from oracle import OracleSim
-    p = params[0]
-    sim = OracleSim(p)
-    cells = p["nx"] * p["ny"]
+    sim, p, what = oracle_sample(params)
+    cells = cells_of(dict(p, dim=params[0].get("dim", 2)))
     sim.step(args.warmup)
     t0 = time.perf_counter()
     sim.step(args.steps)
     dt = time.perf_counter() - t0
     value = cells * args.steps / dt / 1e6
-    sample = ("each step: one time step of lattice 0 (%dx%d) of the workload, FP64 oracle, "
-              "single-threaded C" % (p["nx"], p["ny"]))
+    sample = "each step: one time step of %s, FP64 oracle, single-threaded C" % what
     print(json.dumps({
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
@@ -177,7 +215,8 @@ def run_native(args):
     from paper_1702_04487_gb300 import inkjet
 
     params, desc = workload(args.workload, rank)
-    cells = sum(p["nx"] * p["ny"] for p in params)
+    cells = sum(cells_of(p) for p in params)
+    kind = lattice_kind(params[0])
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -205,8 +244,9 @@ def run_native(args):
     # the step kernel's own launch durations: CUDA events recorded on the
     # handle's stream around every step-kernel launch of a second timed run
     # (launch by launch, so outside the graph replay)
+    k_steps = min(args.steps, 200)
     inkjet.ij_kernel_timing(h, 1)
-    inkjet.ij_step(h, min(args.steps, 200))
+    inkjet.ij_step(h, k_steps)
     k_ms, k_launches = inkjet.ij_kernel_timing(h, 0)
     clk = clocks.stop()
     obs, _ = inkjet.ij_observe(h, 0, phi=False)
@@ -242,30 +282,36 @@ def run_native(args):
 
     if rank == 0:
         peak, peak_kind = measured_peaks()
-        per_launch_ms = k_ms / max(k_launches, 1)
-        launch_cells = cells  # one launch of the step kernel advances every lattice
-        achieved = BYTES_PER_LUP * launch_cells / (per_launch_ms / 1e3) / 1e9
+        # step-kernel time per time step (2-D: one fused launch per bucket;
+        # 3-D: collide3 + stream3 per lattice), against the algorithmic bytes
+        # of one time step of every lattice
+        per_step_ms = k_ms / k_steps
+        bpl = BYTES_PER_LUP[kind]
+        achieved = bpl * cells / (per_step_ms / 1e3) / 1e9
         traffic = None
         rec = NCU_TRAFFIC.get(args.workload)
-        if rec and rec.get("kernel_sha") == kernel_hash():
-            traffic = rec["bytes_per_launch"]
+        if rec and rec.get("kernel_sha") == kernel_hash(params):
+            traffic = rec["bytes_per_step"]
         line = {
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if kind != "3d16" else "f32 (f16 storage)",
             "data": "synthetic",
             "config": {"workload": desc, "lattices": len(params), "cells_per_step": cells,
                        "parallelism": "replicas" if world > 1 else "single",
-                       "l2": "inputs larger than L2 (%.0f MB of state)" % (cells * 56 * 2 / 1e6),
+                       "l2": "inputs larger than L2 (%.0f MB on the device)"
+                             % (sum(device_bytes(p) for p in params) / 1e6),
                        "diag_every": params[0]["diag_every"],
                        "launch": tuning},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind
                          if peak_kind == "measured" else "fallback 6.8 TB/s",
-                         "kernel": "step_kernel", "timed_launches": k_launches,
-                         "ms_per_launch": per_launch_ms,
-                         "algorithmic_bytes_per_launch": BYTES_PER_LUP * launch_cells},
+                         "kernel": "step_kernel" if kind == "2d" else "collide3 + stream3",
+                         "timed_steps": k_steps, "timed_launches": k_launches,
+                         "ms_per_step": per_step_ms, "bytes_per_lup": bpl,
+                         "algorithmic_bytes_per_step": bpl * cells},
             "e2e": {"value": e2e_value, "unit": "MLUPS",
                     "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                     "scope": "ij_create (params in, lattices initialised) + steps + ij_observe of "
@@ -288,7 +334,7 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=("native", "reference"), default="native")
-    ap.add_argument("--workload", choices=("cfg2", "big", "cfg3"), default="cfg2")
+    ap.add_argument("--workload", choices=("cfg2", "big", "cfg3", "cfg4", "cfg4h"), default="cfg2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the default launch shape instead of timing candidates first")

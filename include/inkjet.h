@@ -11,6 +11,17 @@
  * inside a planar nozzle whose inner wall carries a contact angle ("wetting
  * boundary condition", Sect. "Reproducing the experiment").
  *
+ * 3-D lattices (dim = 3) lift the same model to D3Q19 (f) and D3Q7 (g) by
+ * matching the moments of Eq. 5-6 and 9-10; the nozzle is round and its axis
+ * is z.  Their populations are f[i][z][y][x] (i = 0..18) and g[i][z][y][x]
+ * (i = 0..6): rest, +x, -x, +y, -y, +z, -z, then the 12 edge directions
+ * (+x+y, -x+y, +x-y, -x-y, +x+z, -x+z, +x-z, -x-z, +y+z, -y+z, +y-z, -y-z).
+ * Each step is two launches per lattice (collision, then streaming) over a
+ * post-collision copy of the populations; the diagnostics below then run
+ * over z planes (w(z) = sum over x, y of e; mom_y is the sum of n u_z; the
+ * neck criterion needs more than pi R^2 of run ink above).  All lattices of
+ * a handle have the same dim.
+ *
  * Conventions for every entry point:
  *  - All quantities are lattice units (delta x = delta t = 1).
  *  - Every call returns an ij_status and never aborts the process.
@@ -68,7 +79,9 @@ typedef enum {
 #define IJ_INIT_UNIFORM 3  /* phi = init_r everywhere */
 
 /* population storage */
-#define IJ_FP32 0
+#define IJ_FP32 0        /* f as FP32 deviations f_i - w_i n0, g as FP32 */
+#define IJ_FP16_STORE 1  /* 3-D only: f deviations and g_1.. in FP16, g_0 in FP32;
+                            every update is computed in FP32 */
 
 typedef struct {
   int nx, ny;                 /* lattice size, nx, ny >= 1 */
@@ -88,7 +101,12 @@ typedef struct {
   double jitter;              /* amplitude of the meniscus jitter (SplitMix64 of seed, x, y) */
   unsigned long long seed;
   int diag_every;             /* steps between diagnostics records (0: none) */
-  int precision;              /* IJ_FP32 */
+  int precision;              /* IJ_FP32 | IJ_FP16_STORE */
+  int dim;                    /* 2 (D2Q9/D2Q5) or 3 (D3Q19/D3Q7); 0 means 2 */
+  int nz;                     /* 3-D: lattice depth along the nozzle axis z (then the
+                                 axis is z, x and y periodic, nozzle_width is the radius
+                                 of a round nozzle centred at ((nx-1)/2, (ny-1)/2)) */
+  double init_z;              /* 3-D: drop centre z for IJ_INIT_DROP */
 } ij_params;
 
 /* One diagnostics record, evaluated on the state at time `step` (before
@@ -145,7 +163,7 @@ ij_status ij_step(ij_handle h, long long nsteps);
 /*
  * ij_observe -- synchronise, then return the latest diagnostics record of
  * lattice `index` in *out (may be NULL) and its order parameter
- * phi = sum_i g_i (ny*nx floats, solid cells 0) into phi_out (may be NULL;
+ * phi = sum_i g_i (ny*nx floats, 3-D: nz*ny*nx; solid cells 0) into phi_out (may be NULL;
  * device pointer if phi_on_device, else host).  Returns IJ_ERR_NUMERIC (with
  * the outputs filled) if this lattice is frozen by a numeric failure.
  */
@@ -157,8 +175,10 @@ ij_status ij_observe(ij_handle h, int index, ij_obs* out, float* phi_out, int ph
 ij_status ij_history(ij_handle h, int index, double* out, int max_records, int* count);
 
 /* ij_get_state / ij_set_state -- copy the populations of lattice `index`
- * (f: 9*ny*nx floats, g: 5*ny*nx floats, layout above) out of / into the
- * handle; set_state also sets the time to t.  Host or device buffers. */
+ * (f: 9*ny*nx floats, g: 5*ny*nx floats, layout above; 3-D: f 19*nz*ny*nx,
+ * g 7*nz*ny*nx) out of / into the handle as absolute FP32 values (FP16
+ * storage is widened on the way out and rounded on the way in); set_state
+ * also sets the time of the handle to t.  Host or device buffers. */
 ij_status ij_get_state(ij_handle h, int index, float* f, float* g, int on_device);
 ij_status ij_set_state(ij_handle h, int index, const float* f, const float* g, long long t,
                        int on_device);
@@ -192,6 +212,8 @@ ij_status ij_kernel_timing(ij_handle h, int enable, double* total_ms, long long*
  *                 time unchanged.  Synchronises.
  * ij_get_tuning -- block size, chunk, prefetch and item count of bucket
  *                 `bucket` (0-based); IJ_ERR_PARAM past the last bucket.
+ * 3-D handles have one fixed launch shape and no buckets: ij_tune returns
+ * IJ_ERR_PARAM, ij_autotune does nothing.
  */
 ij_status ij_tune(ij_handle h, int block_size, int chunk, int prefetch);
 /* ij_use_graph -- run whole diagnostics periods (diag_every steps, or 16
@@ -212,7 +234,8 @@ ij_status ij_get_tuning(ij_handle h, int bucket, int* block_size, int* chunk, in
  * fixed memory footprint, or code running while its stream is recorded, where
  * cudaMalloc is not allowed.  It computes exactly what ij_step computes for a
  * one-lattice handle.
- *   params        : the lattice (host memory); nx, ny, geometry as in ij_create.
+ *   params        : the lattice (host memory); nx, ny, geometry as in ij_create;
+ *                   2-D only (dim 3 returns IJ_ERR_PARAM).
  *   t             : time of the input state (selects the drive F(t)).
  *   f_in, g_in    : device, the state at t.  f holds the stored layout
  *                   f_i - w_i n0 on fluid cells (n0 = (rho_ink + rho_air)/2,

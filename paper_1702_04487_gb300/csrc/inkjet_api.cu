@@ -12,6 +12,7 @@
 
 #include "inkjet.h"
 #include "lbm2d.cuh"
+#include "lbm3d.cuh"
 
 namespace ij {
 cudaError_t set_step_smem_limit();
@@ -65,6 +66,14 @@ struct Bucket {
 
 struct ij_handle_s {
   int n_inst = 0;
+  // 3-D handles: per-lattice descriptors; `inst` then holds each lattice's
+  // diagnostics descriptor over its z planes (ny = nz) for the shared
+  // record kernel and the observation calls
+  bool is3d = false;
+  std::vector<Inst3> inst3;
+  Inst3* d_inst3 = nullptr;
+  float* stage3 = nullptr;  // FP32 staging of exported / imported 3-D states
+  size_t stage3_floats = 0;
   std::vector<ij_params> params;
   std::vector<Inst> inst;
   std::vector<Item> items;
@@ -159,15 +168,31 @@ ij_status validate(const ij_params& p, int k) {
   if (p.geometry < 0 || p.geometry > 2) return fail(IJ_ERR_PARAM, "lattice %d: bad geometry", k);
   if (p.axial_bc < 0 || p.axial_bc > 2) return fail(IJ_ERR_PARAM, "lattice %d: bad axial_bc", k);
   if (p.init_kind < 0 || p.init_kind > 3) return fail(IJ_ERR_PARAM, "lattice %d: bad init_kind", k);
-  if (p.precision != IJ_FP32) return fail(IJ_ERR_PARAM, "lattice %d: unsupported precision", k);
+  const int dim = p.dim == 0 ? 2 : p.dim;
+  if (dim != 2 && dim != 3) return fail(IJ_ERR_PARAM, "lattice %d: dim must be 2 or 3", k);
+  if (p.precision != IJ_FP32 && !(dim == 3 && p.precision == IJ_FP16_STORE))
+    return fail(IJ_ERR_PARAM, "lattice %d: unsupported precision (FP16 storage is 3-D only)", k);
+  if (dim == 3) {
+    if (p.nz < 1) return fail(IJ_ERR_PARAM, "lattice %d: nz must be >= 1", k);
+    if (p.nz > 65533 || p.ny > 262140)  // grid limits of the 32 x 4 x 1 blocks
+      return fail(IJ_ERR_PARAM, "lattice %d: nz must be <= 65533 and ny <= 262140", k);
+    if ((long long)p.nx * p.ny * p.nz > (1LL << 31) / 19)
+      return fail(IJ_ERR_PARAM, "lattice %d: nx*ny*nz too large", k);
+    if (p.geometry == IJ_GEOM_NOZZLE &&
+        (p.nozzle_width < 1 || p.wall_thickness < 1 || p.nozzle_length < 0 ||
+         2 * (p.nozzle_width + p.wall_thickness) + 4 > std::min(p.nx, p.ny)))
+      return fail(IJ_ERR_PARAM, "lattice %d: round nozzle (radius + wall, plus 2 cells) must fit in nx, ny", k);
+    if (p.geometry == IJ_GEOM_PLATE && (p.wall_thickness < 1 || p.wall_thickness >= p.nz))
+      return fail(IJ_ERR_PARAM, "lattice %d: plate thickness must be in [1, nz)", k);
+  }
   if (p.T1 < 0 || p.T2 < 0 || p.T_idle < 0) return fail(IJ_ERR_PARAM, "lattice %d: negative durations", k);
   if (p.diag_every < 0) return fail(IJ_ERR_PARAM, "lattice %d: diag_every < 0", k);
-  if (p.geometry == IJ_GEOM_NOZZLE) {
+  if (dim == 2 && p.geometry == IJ_GEOM_NOZZLE) {
     if (p.nozzle_width < 1 || p.wall_thickness < 1 || p.nozzle_length < 0 ||
         p.nozzle_width + 2 * p.wall_thickness > p.nx)
       return fail(IJ_ERR_PARAM, "lattice %d: nozzle (width + 2 walls) must fit in nx", k);
   }
-  if (p.geometry == IJ_GEOM_PLATE && (p.wall_thickness < 1 || p.wall_thickness >= p.ny))
+  if (dim == 2 && p.geometry == IJ_GEOM_PLATE && (p.wall_thickness < 1 || p.wall_thickness >= p.ny))
     return fail(IJ_ERR_PARAM, "lattice %d: plate thickness must be in [1, ny)", k);
   return IJ_OK;
 }
@@ -226,6 +251,59 @@ Inst derive(const ij_params& p) {
   I.y_exit = nozzle ? p.nozzle_length : 0;
   I.y_scan = nozzle ? p.nozzle_length - p.nozzle_length / 2 : 0;
   I.vmin = nozzle ? (double)p.nozzle_width : 1.0;
+  return I;
+}
+
+// Derived constants of one 3-D lattice (same closure as derive()).
+Inst3 derive3(const ij_params& p) {
+  const Inst I2 = derive(p);
+  Inst3 I;
+  memset(&I, 0, sizeof(I));
+  I.nx = p.nx;
+  I.ny = p.ny;
+  I.nz = p.nz;
+  I.geom = p.geometry;
+  I.L = p.nozzle_length;
+  I.wt = p.wall_thickness;
+  I.bc = p.axial_bc;
+  I.fp16 = p.precision == IJ_FP16_STORE;
+  I.cx = 0.5f * (p.nx - 1);
+  I.cy = 0.5f * (p.ny - 1);
+  I.R2 = (float)p.nozzle_width * (float)p.nozzle_width;
+  I.Ro2 = (float)(p.nozzle_width + p.wall_thickness) * (float)(p.nozzle_width + p.wall_thickness);
+  I.phis = I2.phis;
+  I.inv_phis = I2.inv_phis;
+  I.A4 = I2.A4;
+  I.kappa = I2.kappa;
+  I.hk = I2.hk;
+  I.q = I2.q;
+  I.omq = I2.omq;
+  I.inv_tphi = I2.inv_tphi;
+  I.gamma = I2.gamma;
+  I.inv2q = I2.inv2q;
+  I.nu_air = I2.nu_air;
+  I.dnu = I2.dnu;
+  I.F0 = I2.F0;
+  I.Fneg = I2.Fneg;
+  I.n0 = I2.n0;
+  I.T1 = p.T1;
+  I.T2 = p.T2;
+  I.Tidle = p.T_idle;
+  I.d_phis = I2.d_phis;
+  I.d_n0 = I2.d_n0;
+  I.d_A = I2.d_A;
+  I.d_kappa = I2.d_kappa;
+  I.d_h = I2.d_h;
+  I.d_gamma = I2.d_gamma;
+  I.d_q = I2.d_q;
+  I.d_W = I2.d_W;
+  I.init_x = p.init_x;
+  I.init_y = p.init_y;
+  I.init_z = p.init_z;
+  I.init_r = p.init_r;
+  I.jitter = p.jitter;
+  I.init_kind = p.init_kind;
+  I.seed = p.seed;
   return I;
 }
 
@@ -298,8 +376,55 @@ ij_status check_handle(ij_handle h) {
   return IJ_OK;
 }
 
+// One 3-D time step on stream s: the collisions of every lattice (with
+// plane sums when diag), the diagnostics record, the streamings.
+cudaError_t enqueue_step3(ij_handle h, cudaStream_t s, int t_off, bool diag, long long* n) {
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < h->n_inst && e == cudaSuccess; k++, (*n)++) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (h->timing) {
+      e0 = h->get_event();
+      e1 = h->get_event();
+      cudaEventRecord(e0, s);
+    }
+    e = launch_collide3(h->d_inst3, h->inst3[k], k, h->d_t, t_off, diag, s);
+    if (h->timing) {
+      cudaEventRecord(e1, s);
+      h->events.push_back({e0, e1});
+      h->timed_launches++;
+    }
+  }
+  if (diag && e == cudaSuccess) {
+    e = launch_finalize(h->d_inst, h->n_inst, h->d_t, s);
+    (*n)++;
+  }
+  for (int k = 0; k < h->n_inst && e == cudaSuccess; k++, (*n)++) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (h->timing) {
+      e0 = h->get_event();
+      e1 = h->get_event();
+      cudaEventRecord(e0, s);
+    }
+    e = launch_stream3(h->d_inst3, h->inst3[k], k, s);
+    if (h->timing) {
+      cudaEventRecord(e1, s);
+      h->events.push_back({e0, e1});
+    }
+  }
+  return e;
+}
+
 ij_status one_step(ij_handle h) {
   const bool diag = h->diag_every > 0 && h->t % h->diag_every == 0;
+  if (h->is3d) {
+    long long n = 0;
+    CUDA_TRY(enqueue_step3(h, h->stream, 0, diag, &n));
+    h->launches += n;
+    CUDA_TRY(launch_advance(h->d_t, 1, h->stream));
+    h->launches++;
+    h->t++;
+    return IJ_OK;
+  }
   for (const Bucket& b : h->buckets) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (h->timing) {
@@ -339,6 +464,10 @@ ij_status build_graph(ij_handle h) {
   cudaError_t e = cudaSuccess;
   for (int j = 0; j < P && e == cudaSuccess; j++) {
     const bool diag = h->diag_every > 0 && j == 0;
+    if (h->is3d) {
+      e = enqueue_step3(h, cs, j, diag, &n);
+      continue;
+    }
     for (const Bucket& b : h->buckets) {
       e = launch_step(h->d_inst, h->d_items + b.first, b.count, b.nthreads, b.grid, h->d_t, j,
                       diag, b.prefetch, cs);
@@ -365,6 +494,121 @@ ij_status build_graph(ij_handle h) {
   if (e != cudaSuccess) return fail(IJ_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
   h->graph_steps = P;
   h->graph_launches = n;
+  return IJ_OK;
+}
+
+// Allocate and initialise the lattices of a 3-D handle.
+ij_status create3(ij_handle h) {
+  const int count = h->n_inst;
+  h->is3d = true;
+  h->inst3.resize(count);
+  h->inst.resize(count);
+  for (int k = 0; k < count; k++) {
+    const ij_params& p = h->params[k];
+    Inst3 I = derive3(p);
+    const size_t N = (size_t)p.nx * p.ny * p.nz, NP = (size_t)p.nx * p.ny * (p.nz + 2);
+    const size_t es = I.fp16 ? 2 : 4;
+    I.f = h->dalloc(19 * N * es);
+    I.g = h->dalloc(6 * N * es);
+    I.g0 = (float*)h->dalloc(N * sizeof(float));
+    I.fp = h->dalloc(std::max(19 * NP * es, N * sizeof(double)));
+    I.gp = h->dalloc(6 * NP * es);
+    I.g0p = (float*)h->dalloc(NP * sizeof(float));
+    I.phi = (float*)h->dalloc(N * sizeof(float));
+    // diagnostics over z planes, in the 2-D descriptor the record kernel reads
+    Inst D;
+    memset(&D, 0, sizeof(D));
+    D.nx = p.nx;
+    D.ny = p.nz;
+    const bool nozzle = p.geometry == IJ_GEOM_NOZZLE;
+    D.y_exit = nozzle ? p.nozzle_length : 0;
+    D.y_scan = nozzle ? p.nozzle_length - p.nozzle_length / 2 : 0;
+    D.vmin = nozzle ? M_PI * p.nozzle_width * p.nozzle_width : 1.0;
+    D.rows = (double*)h->dalloc(3 * (size_t)p.nz * sizeof(double));
+    D.sums = (double*)h->dalloc(4 * sizeof(double));
+    D.hist = (double*)h->dalloc((size_t)kHistCap * kRec * sizeof(double));
+    D.dstate = (double*)h->dalloc(8 * sizeof(double));
+    if (!I.f || !I.g || !I.g0 || !I.fp || !I.gp || !I.g0p || !I.phi || !D.rows || !D.sums ||
+        !D.hist || !D.dstate)
+      return fail(IJ_ERR_OOM, "device allocation of 3-D lattice %d failed", k);
+    I.rows = D.rows;
+    I.sums = D.sums;
+    h->inst3[k] = I;
+    h->inst[k] = D;
+  }
+  h->d_inst3 = (Inst3*)h->dalloc(count * sizeof(Inst3));
+  h->d_inst = (Inst*)h->dalloc(count * sizeof(Inst));
+  h->d_t = (long long*)h->dalloc(sizeof(long long));
+  h->d_status = (unsigned*)h->dalloc(count * sizeof(unsigned));
+  if (!h->d_inst3 || !h->d_inst || !h->d_t || !h->d_status)
+    return fail(IJ_ERR_OOM, "device allocation of descriptors failed");
+  for (int k = 0; k < count; k++) h->inst3[k].status = h->inst[k].status = h->d_status + k;
+  if (cudaMallocHost((void**)&h->h_status, count * sizeof(unsigned)) != cudaSuccess)
+    return fail(IJ_ERR_OOM, "pinned allocation failed");
+  memset(h->h_status, 0, count * sizeof(unsigned));
+  cudaStream_t s = h->stream;
+  CUDA_TRY(cudaMemcpyAsync(h->d_inst3, h->inst3.data(), count * sizeof(Inst3), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(h->d_inst, h->inst.data(), count * sizeof(Inst), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemsetAsync(h->d_t, 0, sizeof(long long), s));
+  CUDA_TRY(cudaMemsetAsync(h->d_status, 0, count * sizeof(unsigned), s));
+  const double dinit[8] = {0, 0, 0, -1, 0, 0, 0, 0};
+  for (int k = 0; k < count; k++) {
+    const Inst& D = h->inst[k];
+    CUDA_TRY(cudaMemsetAsync(D.rows, 0, 3 * (size_t)D.ny * sizeof(double), s));
+    CUDA_TRY(cudaMemsetAsync(D.sums, 0, 4 * sizeof(double), s));
+    CUDA_TRY(cudaMemsetAsync(D.hist, 0, (size_t)kHistCap * kRec * sizeof(double), s));
+    CUDA_TRY(cudaMemcpyAsync(D.dstate, dinit, sizeof(dinit), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(launch_init3(h->d_inst3, h->inst3[k], k, s));
+    h->launches += 2;
+  }
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return IJ_OK;
+}
+
+// FP32 staging buffer for exporting / importing a 3-D lattice's state.
+ij_status ensure_stage3(ij_handle h, size_t floats) {
+  if (h->stage3_floats >= floats) return IJ_OK;
+  h->stage3 = (float*)h->dalloc(floats * sizeof(float));
+  if (!h->stage3) return fail(IJ_ERR_OOM, "device allocation of the 3-D staging buffer failed");
+  h->stage3_floats = floats;
+  return IJ_OK;
+}
+
+// Absolute FP32 populations of a 3-D lattice: f [19][N], g [7][N].
+ij_status get_state3(ij_handle h, int index, float* f, float* g, int on_device) {
+  const Inst3& J = h->inst3[index];
+  const size_t N = (size_t)J.nx * J.ny * J.nz;
+  ij_status st = ensure_stage3(h, 26 * N);
+  if (st != IJ_OK) return st;
+  CUDA_TRY(launch_export3(h->d_inst3, J, index, h->stage3, h->stage3 + 19 * N, h->stream));
+  h->launches++;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (f) CUDA_TRY(cudaMemcpyAsync(f, h->stage3, 19 * N * sizeof(float), kind, h->stream));
+  if (g) CUDA_TRY(cudaMemcpyAsync(g, h->stage3 + 19 * N, 7 * N * sizeof(float), kind, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return IJ_OK;
+}
+
+// The 3-D state is not double-buffered by time parity, so setting one
+// lattice's time needs no move of the others' state.
+ij_status set_state3(ij_handle h, int index, const float* f, const float* g, long long t,
+                     int on_device) {
+  const Inst3& J = h->inst3[index];
+  const size_t N = (size_t)J.nx * J.ny * J.nz;
+  ij_status st = ensure_stage3(h, 26 * N);
+  if (st != IJ_OK) return st;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CUDA_TRY(cudaMemcpyAsync(h->stage3, f, 19 * N * sizeof(float), kind, h->stream));
+  CUDA_TRY(cudaMemcpyAsync(h->stage3 + 19 * N, g, 7 * N * sizeof(float), kind, h->stream));
+  CUDA_TRY(launch_import3(h->d_inst3, J, index, h->stage3, h->stage3 + 19 * N, h->stream));
+  h->launches++;
+  CUDA_TRY(cudaMemcpyAsync(h->d_t, &t, sizeof(long long), cudaMemcpyHostToDevice, h->stream));
+  const double dinit[8] = {0, 0, 0, -1, 0, 0, 0, 0};
+  for (int k = 0; k < h->n_inst; k++)
+    CUDA_TRY(cudaMemcpyAsync(h->inst[k].dstate, dinit, sizeof(dinit), cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  h->t = t;
+  h->drop_graph();
   return IJ_OK;
 }
 
@@ -410,6 +654,16 @@ ij_status ij_create(const ij_params* params, int count, ij_alloc_fn alloc, ij_fr
   };
   cudaError_t e = set_step_smem_limit();
   if (e != cudaSuccess) return bail(fail(IJ_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e)));
+  const int dim0 = params[0].dim == 0 ? 2 : params[0].dim;
+  for (int k = 0; k < count; k++)
+    if ((params[k].dim == 0 ? 2 : params[k].dim) != dim0)
+      return bail(fail(IJ_ERR_PARAM, "all lattices of a batch must have the same dim"));
+  if (dim0 == 3) {
+    ij_status st3 = create3(h);
+    if (st3 != IJ_OK) return bail(st3);
+    *out = h;
+    return IJ_OK;
+  }
   h->inst.resize(count);
   for (int k = 0; k < count; k++) {
     Inst I = derive(params[k]);
@@ -507,8 +761,20 @@ ij_status ij_observe(ij_handle h, int index, ij_obs* out, float* phi_out, int ph
   if (st != IJ_OK) return st;
   if (index < 0 || index >= h->n_inst) return fail(IJ_ERR_PARAM, "index out of range");
   const Inst& I = h->inst[index];
-  const size_t N = (size_t)I.nx * I.ny;
-  if (phi_out) {
+  if (phi_out && h->is3d) {
+    const Inst3& J = h->inst3[index];
+    const size_t N3 = (size_t)J.nx * J.ny * J.nz;
+    if (!phi_on_device) {
+      st = ensure_stage3(h, N3);
+      if (st != IJ_OK) return st;
+    }
+    float* dst = phi_on_device ? phi_out : h->stage3;
+    CUDA_TRY(launch_phi3(h->d_inst3, J, index, dst, h->stream));
+    h->launches++;
+    if (!phi_on_device)
+      CUDA_TRY(cudaMemcpyAsync(phi_out, dst, N3 * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+  } else if (phi_out) {
+    const size_t N = (size_t)I.nx * I.ny;
     float* dst = phi_on_device ? phi_out : h->inst[index].f[(h->t + 1) & 1];
     CUDA_TRY(launch_phi(h->d_inst, I, index, h->d_t, dst, h->stream));
     h->launches++;
@@ -562,6 +828,7 @@ ij_status ij_get_state(ij_handle h, int index, float* f, float* g, int on_device
   ij_status st = check_handle(h);
   if (st != IJ_OK) return st;
   if (index < 0 || index >= h->n_inst) return fail(IJ_ERR_PARAM, "index out of range");
+  if (h->is3d) return get_state3(h, index, f, g, on_device);
   const Inst& I = h->inst[index];
   const size_t N = (size_t)I.nx * I.ny;
   cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
@@ -588,6 +855,7 @@ ij_status ij_set_state(ij_handle h, int index, const float* f, const float* g, l
   if (h->poisoned) return fail(IJ_ERR_STATE, "handle is poisoned");
   if (!f || !g) return fail(IJ_ERR_PARAM, "f and g are required");
   CUDA_TRY(cudaStreamSynchronize(h->stream));
+  if (h->is3d) return set_state3(h, index, f, g, t, on_device);
   cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   // all lattices share the time: move the others' state to the new parity
   if ((t & 1) != (h->t & 1)) {
@@ -649,6 +917,7 @@ ij_status ij_kernel_timing(ij_handle h, int enable, double* total_ms, long long*
 ij_status ij_tune(ij_handle h, int block_size, int chunk, int prefetch) {
   ij_status st = check_handle(h);
   if (st != IJ_OK) return st;
+  if (h->is3d) return fail(IJ_ERR_PARAM, "3-D handles have no launch shape to tune");
   if (chunk < 1 || (prefetch != 1 && prefetch != 2))
     return fail(IJ_ERR_PARAM, "chunk must be >= 1 and prefetch 1 or 2");
   bool found = false;
@@ -675,6 +944,7 @@ ij_status ij_autotune(ij_handle h, int reps) {
   if (st != IJ_OK) return st;
   if (reps < 1) return fail(IJ_ERR_PARAM, "reps must be >= 1");
   if (h->poisoned) return fail(IJ_ERR_STATE, "handle is poisoned");
+  if (h->is3d) return IJ_OK;  // the 3-D kernels have one fixed launch shape
   static const int kChunks[] = {8, 16, 24, 32, 48, 64, 96, 128, 192};
   cudaEvent_t e0, e1;
   CUDA_TRY(cudaEventCreate(&e0));

@@ -85,6 +85,7 @@ extern "C" ij_status ij_step_noalloc(const ij_params* params, long long t, const
   ij_status st = validate_params(*params, 0);
   if (st != IJ_OK) return st;
   const ij_params& p = *params;
+  if (p.dim == 3) return report(IJ_ERR_PARAM, "ij_step_noalloc: 2-D lattices only");
   if (p.ny > kMaxRows)
     return report(IJ_ERR_PARAM, "ij_step_noalloc: ny exceeds the fixed scratch limit of 8192 rows");
   // work list: the same strips and row chunks ij_create builds for one lattice

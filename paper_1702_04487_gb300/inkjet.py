@@ -48,6 +48,9 @@ class ij_params(C.Structure):
         ("seed", C.c_ulonglong),
         ("diag_every", C.c_int),
         ("precision", C.c_int),
+        ("dim", C.c_int),
+        ("nz", C.c_int),
+        ("init_z", C.c_double),
     ]
 
 
@@ -59,7 +62,7 @@ DEFAULTS = dict(nx=8, ny=8, geometry=0, nozzle_width=0, nozzle_length=0, wall_th
                 rho_ink=10.0, rho_air=1.0, nu_ink=0.1, nu_air=0.05, sigma=0.01, width_W=3.0,
                 tau_phi=0.8, gamma=0.0, theta_deg=90.0, F0=0.0, F_neg=0.0, T1=0, T2=0,
                 T_idle=0, axial_bc=0, init_kind=0, init_x=0.0, init_y=0.0, init_r=0.0,
-                jitter=1e-6, seed=0, diag_every=0, precision=0)
+                jitter=1e-6, seed=0, diag_every=0, precision=0, dim=2, nz=1, init_z=0.0)
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
@@ -108,6 +111,18 @@ def _lattice(h, index):
         return h.lattices[index]
     _check(_lib.ij_get_state(h.ptr, int(index), None, None, 0))
     raise InkjetError(IJ_ERR_PARAM, "index out of range")
+
+
+def _grid(p):
+    """Cell-array shape of a lattice: (ny, nx), or (nz, ny, nx) in 3-D."""
+    if p.get("dim", 2) == 3:
+        return (p["nz"], p["ny"], p["nx"])
+    return (p["ny"], p["nx"])
+
+
+def _nq(p):
+    """Number of f and g directions: D2Q9/D2Q5 or D3Q19/D3Q7."""
+    return (19, 7) if p.get("dim", 2) == 3 else (9, 5)
 
 
 def _check(status):
@@ -176,17 +191,23 @@ def ij_step(h, nsteps):
 
 
 def ij_observe(h, index=0, phi=True):
-    """Latest diagnostics record (dict) and phi as a numpy (ny, nx) array."""
+    """Latest diagnostics record (dict) and phi as a numpy (ny, nx) array
+    ((nz, ny, nx) in 3-D)."""
     obs = ij_obs()
     p = _lattice(h, index)
-    arr = np.empty((p["ny"], p["nx"]), dtype=np.float32) if phi else None
+    arr = np.empty(_grid(p), dtype=np.float32) if phi else None
     _check(_lib.ij_observe(h.ptr, index, C.byref(obs),
                            arr.ctypes.data_as(C.c_void_p) if phi else None, 0))
     return {k: getattr(obs, k) for k in REC_FIELDS}, arr
 
 
 def ij_observe_device(h, index, phi_tensor):
-    """Write phi of lattice ``index`` into a float32 CUDA tensor (ny, nx)."""
+    """Write phi of lattice ``index`` into a float32 CUDA tensor (ny, nx)
+    ((nz, ny, nx) in 3-D)."""
+    p = _lattice(h, index)
+    if (tuple(phi_tensor.shape) != _grid(p) or not phi_tensor.is_contiguous()
+            or str(phi_tensor.dtype) != "torch.float32" or not phi_tensor.is_cuda):
+        raise ValueError("phi must be a contiguous float32 CUDA tensor of shape %s" % (_grid(p),))
     obs = ij_obs()
     _check(_lib.ij_observe(h.ptr, index, C.byref(obs), C.c_void_p(phi_tensor.data_ptr()), 1))
     return {k: getattr(obs, k) for k in REC_FIELDS}
@@ -202,16 +223,21 @@ def ij_history(h, index=0):
 
 def ij_get_state(h, index=0):
     p = _lattice(h, index)
-    f = np.empty((9, p["ny"], p["nx"]), dtype=np.float32)
-    g = np.empty((5, p["ny"], p["nx"]), dtype=np.float32)
+    qf, qg = _nq(p)
+    f = np.empty((qf,) + _grid(p), dtype=np.float32)
+    g = np.empty((qg,) + _grid(p), dtype=np.float32)
     _check(_lib.ij_get_state(h.ptr, index, f.ctypes.data_as(C.c_void_p),
                              g.ctypes.data_as(C.c_void_p), 0))
     return f, g
 
 
 def ij_set_state(h, index, f, g, t):
+    p = _lattice(h, index)
+    qf, qg = _nq(p)
     f = np.ascontiguousarray(f, dtype=np.float32)
     g = np.ascontiguousarray(g, dtype=np.float32)
+    if f.shape != (qf,) + _grid(p) or g.shape != (qg,) + _grid(p):
+        raise ValueError("state shapes must be %s and %s" % ((qf,) + _grid(p), (qg,) + _grid(p)))
     _check(_lib.ij_set_state(h.ptr, index, f.ctypes.data_as(C.c_void_p),
                              g.ctypes.data_as(C.c_void_p), int(t), 0))
 

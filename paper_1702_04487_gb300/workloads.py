@@ -106,3 +106,43 @@ def small_nozzle(nx=48, ny=96, **kw):
              init_kind=INIT_MENISCUS, jitter=1e-6, seed=1, diag_every=10)
     p.update(kw)
     return p
+
+
+def cfg4(theta_deg=60.0, precision=0, nx=128, ny=128, nz=640, radius=24, length=160, wall=10,
+         seed=4):
+    """3-D round nozzle (D3Q19/D3Q7): 128 x 128 x 640, radius 24, length 160,
+    wall 10, axis z.  Drive drawn as in the 200 x 1600 sweep (F0 ~ U[1e-4,
+    4e-4], T1, T2 ~ U{500..3000}, negative pulse F0 / 2) from ``seed``.
+    ``precision`` 0 stores populations in FP32, 1 in FP16 (offsets)."""
+    rng = np.random.default_rng(seed)
+    F0 = float(rng.uniform(1e-4, 4e-4))
+    T1 = int(rng.integers(500, 3001))
+    T2 = int(rng.integers(500, 3001))
+    return dict(dim=3, nx=nx, ny=ny, nz=nz, geometry=GEOM_NOZZLE, nozzle_width=radius,
+                nozzle_length=length, wall_thickness=wall, rho_ink=10.0, rho_air=1.0,
+                nu_ink=0.1, nu_air=0.05, sigma=SIGMA_BASE, width_W=3.0, tau_phi=0.8, gamma=0.0,
+                theta_deg=theta_deg, F0=F0, F_neg=F0 / 2, T1=T1, T2=T2, T_idle=0,
+                axial_bc=BC_ZERO_GRADIENT, init_kind=INIT_MENISCUS, jitter=1e-6, seed=seed,
+                diag_every=10, precision=precision)
+
+
+def cfg4_downscale(theta_deg=60.0, precision=0):
+    """The 3-D round nozzle at a quarter of the size: 32 x 32 x 160, radius
+    6, length 40, wall 3, same drive."""
+    return cfg4(theta_deg, precision, nx=32, ny=32, nz=160, radius=6, length=40, wall=3)
+
+
+def small_nozzle3(nx=20, ny=20, nz=64, **kw):
+    """A small 3-D round nozzle for quick checks: radius 5, length 16,
+    wall 2, ink viscosity 0.05 and a strong drive (+1e-2 for 600 steps,
+    -5e-3 for 400): the jet reaches the top and its neck pinches off near
+    step 1330."""
+    p = dict(dim=3, nx=nx, ny=ny, nz=nz, geometry=GEOM_NOZZLE, nozzle_width=5,
+             nozzle_length=16, wall_thickness=2, rho_ink=10.0, rho_air=1.0, nu_ink=0.05,
+             nu_air=0.05, sigma=SIGMA_BASE / 4, width_W=3.0, tau_phi=0.8, gamma=0.0,
+             theta_deg=60.0, F0=1e-2, F_neg=5e-3, T1=600, T2=400, T_idle=0,
+             axial_bc=BC_ZERO_GRADIENT, init_kind=INIT_MENISCUS, jitter=1e-6, seed=5,
+             diag_every=10, precision=0)
+    p.update(kw)
+    return p
+

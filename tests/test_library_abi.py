@@ -62,4 +62,4 @@ def test_binding_and_oracle_share_only_the_parameter_names():
     lib_fields = [f[0] for f in inkjet.ij_params._fields_]
     orc_fields = [f[0] for f in _Params._fields_]
     assert set(orc_fields) <= set(lib_fields)
-    assert set(lib_fields) - set(orc_fields) == {"precision"}
+    assert set(lib_fields) - set(orc_fields) == {"precision", "dim"}

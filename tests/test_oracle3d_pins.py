@@ -121,3 +121,26 @@ def test_flat_interface3_profile():
     phi = s.state()[1].sum(0)[:, 0, 0]
     z = np.arange(60)
     assert np.abs(phi - 4.5 * np.tanh((30 - z) / 3.0)).max() < 0.01 * 4.5
+
+
+@pytest.mark.slow
+def test_fp32_noise_floor_of_small_nozzle3():
+    """The round-off floor that bounds any FP32 implementation of the small
+    3-D round nozzle: an oracle run that takes a relative 2^-24 (FP32
+    rounding) perturbation of every population after every step ends, at
+    step 1000, 1.3-2.0e-5 of phi* from the exact run (seeds 12, 13; at step
+    600, while the jet leaves through the top, the two differ by 2e-2).  The
+    GPU parity bound on phi at step 1000 (6e-5) stays at about three times
+    this floor."""
+    p = {k: v for k, v in W.small_nozzle3().items() if k not in ("dim", "precision")}
+    ref, noisy = OracleSim3(p), OracleSim3(p)
+    rng = np.random.default_rng(12)
+    eps = 2.0 ** -24
+    for t in range(1, 1001):
+        ref.step(1)
+        noisy.step(1)
+        f, g = noisy.state()
+        noisy.set_state(f * (1 + eps * rng.uniform(-1, 1, f.shape)),
+                        g * (1 + eps * rng.uniform(-1, 1, g.shape)), t)
+    d = np.abs(noisy.state()[1].sum(0) - ref.state()[1].sum(0)).max() / 4.5
+    assert 5e-6 < d < 3e-5
