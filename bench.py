@@ -328,6 +328,102 @@ def run_native(args):
         dist.destroy_process_group()
 
 
+def run_surrogate(args):
+    """Sweep throughput of the learned surrogate with its lattice Boltzmann
+    fallback against the lattice Boltzmann model alone (one lattice per
+    handle, and batched), on held-out draws of the surrogate's input box."""
+    import numpy as np
+    import torch
+    from paper_1702_04487_gb300 import surrogate as S
+
+    torch.cuda.set_device(0)
+    steps = args.sg_lbm_steps
+    t0 = time.perf_counter()
+    x_tr = S.sample_inputs(args.sg_train_runs, 41)
+    y_tr = S.lbm_outcomes(x_tr, steps=steps)
+    t_gen = time.perf_counter() - t0
+    ok = S.finite_rows(y_tr)
+    sg = S.Surrogate(members=5, hidden=256, batch=256, seed=5, lr=1e-3)
+    sg.set_data(x_tr[ok], y_tr[ok])
+    t0 = time.perf_counter()
+    loss = sg.train(args.sg_train_steps)
+    t_train = time.perf_counter() - t0
+    sg.set_gate(args.sg_tau, args.sg_tau_v)
+
+    x_ev = S.sample_inputs(args.sg_eval_runs, 43)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    y_ev = S.lbm_outcomes(x_ev, steps=steps)  # batched: every query a lattice of one handle
+    t_batched = time.perf_counter() - t0
+    one = min(8, len(x_ev))
+    t0 = time.perf_counter()
+    for k in range(one):
+        S.lbm_outcomes(x_ev[k:k + 1], steps=steps)
+    t_single = (time.perf_counter() - t0) / one
+    sg.predict(x_ev[:16])  # workspace warm-up
+    svc = S.SurrogateService(sg, lbm_steps=steps)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    y_sv, acc = svc.query(x_ev)
+    t_service = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for _ in range(10):
+        sg.predict(x_ev, gate=True)
+    t_pred = (time.perf_counter() - t0) / 10
+    # accuracy / acceptance trade-off of the spread thresholds (same
+    # predictions, thresholds applied to the returned spreads; the LBM cost
+    # of the rejected queries is taken at the batched rate)
+    m_all, sd_all, _ = sg.predict(x_ev, gate=False)
+    fin_all = S.finite_rows(y_ev)
+    rt = sd_all[:, 0] / np.abs(m_all[:, 0])
+    rv = sd_all[:, 1] / np.maximum(np.abs(m_all[:, 1]), 1e-30)
+    tradeoff = []
+    for tau in (0.002, 0.005, 0.01, 0.02):
+        a = (rt <= tau) & (rv <= 2 * tau)
+        s_ = a & fin_all
+        et = S.relative_error(m_all[s_, 0], y_ev[s_, 0])
+        ev = S.relative_error(m_all[s_, 1], y_ev[s_, 1])
+        rej = len(x_ev) - int(a.sum())
+        t_est = t_pred + rej / (len(x_ev) / t_batched)
+        tradeoff.append({"tau": tau, "tau_v": 2 * tau, "accepted": int(a.sum()),
+                         "accepted_not_ejecting": int((a & ~fin_all).sum()),
+                         "breakup_within_1pct": float((et <= 0.01).mean()) if len(et) else None,
+                         "velocity_within_1pct": float((ev <= 0.01).mean()) if len(ev) else None,
+                         "runs_per_s_est": len(x_ev) / t_est})
+
+    fin = S.finite_rows(y_ev)
+    sel = acc & fin
+    err_tb = S.relative_error(y_sv[sel, 0], y_ev[sel, 0])
+    err_v = S.relative_error(y_sv[sel, 1], y_ev[sel, 1])
+    err_vol = S.relative_error(y_sv[sel, 2], y_ev[sel, 2])
+    n = len(x_ev)
+    line = {
+        "metric": "sweep throughput at <=1% error (surrogate + LBM fallback vs LBM)",
+        "value": n / t_service, "unit": "runs/s", "n_gpus": 1, "higher_is_better": True,
+        "dtype": "bf16 GEMM / f32 LBM", "data": "synthetic",
+        "config": {"workload": "planar nozzle ejection runs, inputs %s" % S.describe_inputs(),
+                   "lbm_steps_per_run": steps, "train_runs": int(len(x_tr)),
+                   "train_runs_ejecting": int(ok.sum()), "eval_runs": n,
+                   "eval_runs_ejecting": int(fin.sum()),
+                   "network": "5 x MLP 7-256-256-256-256-4 GELU, BF16 tcgen05 GEMMs",
+                   "train_steps": args.sg_train_steps, "tau": args.sg_tau},
+        "lbm_single_runs_per_s": 1.0 / t_single,
+        "lbm_batched_runs_per_s": n / t_batched,
+        "surrogate_only_queries_per_s": n / t_pred,
+        "accepted": int(acc.sum()), "accepted_ejecting": int(sel.sum()),
+        "accepted_not_ejecting": int((acc & ~fin).sum()),
+        "error_accepted": {
+            "breakup_p50": float(np.median(err_tb)) if len(err_tb) else None,
+            "breakup_p95": float(np.percentile(err_tb, 95)) if len(err_tb) else None,
+            "velocity_p50": float(np.median(err_v)) if len(err_v) else None,
+            "velocity_p95": float(np.percentile(err_v, 95)) if len(err_v) else None,
+            "volume_p50": float(np.median(err_vol)) if len(err_vol) else None},
+        "tradeoff": tradeoff,
+        "train_loss": loss, "train_s": t_train, "data_generation_s": t_gen,
+    }
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -339,10 +435,20 @@ def main():
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the default launch shape instead of timing candidates first")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--surrogate", action="store_true",
+                    help="measure the surrogate sweep (data generation, training, gated queries)")
+    ap.add_argument("--sg-train-runs", type=int, default=4096)
+    ap.add_argument("--sg-eval-runs", type=int, default=512)
+    ap.add_argument("--sg-train-steps", type=int, default=12000)
+    ap.add_argument("--sg-lbm-steps", type=int, default=5000)
+    ap.add_argument("--sg-tau", type=float, default=0.005)
+    ap.add_argument("--sg-tau-v", type=float, default=0.01)
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
-    if args.impl == "reference":
+    if args.surrogate:
+        run_surrogate(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_native(args)

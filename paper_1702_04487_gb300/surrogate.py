@@ -1,0 +1,286 @@
+"""Surrogate of the inkjet lattice Boltzmann model (include/surrogate.h).
+
+Thin ctypes binding of the sg_* entry points of libinkjet.so, plus the host
+logic of the service around them:
+
+- ``sample_inputs``: seeded draws of the seven surrogate inputs (contact
+  angle, surface tension, F0, T1, T2, idle time, nozzle width) in a regime
+  where the planar nozzle ejects a droplet within a few thousand steps;
+- ``lattice_params``: the lattice of one input row (nozzle w wide, domain
+  4w x 24w, nozzle length 3w, walls 4 -- the uneven-sweep geometry);
+- ``lbm_outcomes``: runs input rows on the batched lattice Boltzmann path
+  (one handle, every row a lattice) and reads breakup time, droplet
+  velocity, droplet volume and satellites from the FP64 diagnostics;
+- ``SurrogateService``: answers queries with the ensemble where the gate
+  accepts them and re-runs the rest on the lattice Boltzmann model.
+
+Every contraction and element-wise step of training and inference runs in
+the library's kernels; this module only marshals arguments and orchestrates
+the two paths.
+"""
+import ctypes as C
+
+import numpy as np
+
+from . import inkjet as ij
+from . import workloads as W
+
+N_IN, N_OUT = 7, 4
+INPUT_NAMES = ("theta_deg", "sigma", "F0", "T1", "T2", "T_idle", "width")
+OUTPUT_NAMES = ("breakup_step", "droplet_velocity", "droplet_volume", "satellites")
+
+
+class sg_config(C.Structure):
+    _fields_ = [("members", C.c_int), ("hidden", C.c_int), ("batch", C.c_int),
+                ("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
+                ("seed", C.c_ulonglong), ("log_inputs", C.c_int), ("log_outputs", C.c_int),
+                ("out_weight", C.c_float * 4)]
+
+
+_lib = ij._lib
+_vp, _i, _fp = C.c_void_p, C.c_int, C.c_void_p
+_sig = {
+    "sg_create": [C.POINTER(sg_config), ij.ALLOC_FN, ij.FREE_FN, _vp, _vp, C.POINTER(_vp)],
+    "sg_set_data": [_vp, _fp, _fp, _i],
+    "sg_train": [_vp, _i, C.POINTER(C.c_double)],
+    "sg_predict": [_vp, _fp, _i, _fp, _fp, _fp, _i],
+    "sg_set_gate": [_vp, C.c_float, C.c_float, C.c_float],
+    "sg_param_count": [_vp, C.POINTER(C.c_longlong)],
+    "sg_get_params": [_vp, _i, _fp],
+    "sg_set_params": [_vp, _i, _fp],
+    "sg_get_transform": [_vp, _fp, _fp, _fp, _fp],
+    "sg_gradients": [_vp, _fp, _fp, _i, _fp, _fp],
+    "sg_destroy": [_vp],
+    "sg_gemm_bf16": [_fp, _i, _fp, _i, _i, _i, _i, _fp, _i, _vp],
+}
+for _name, _args in _sig.items():
+    getattr(_lib, _name).argtypes = _args
+    getattr(_lib, _name).restype = C.c_int
+_lib.sg_last_error.restype = C.c_char_p
+_lib.sg_last_error.argtypes = []
+
+
+def _check(status):
+    if status != ij.IJ_OK:
+        raise ij.InkjetError(status, _lib.sg_last_error().decode())
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def gemm_bf16(A, B, M, N, K, C_out, lda, ldb, ldc, stream=None):
+    """C_out = A B^T on device tensors (A, B bfloat16, C_out float32)."""
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    _check(_lib.sg_gemm_bf16(C.c_void_p(A.data_ptr()), lda, C.c_void_p(B.data_ptr()), ldb, M, N, K,
+                             C.c_void_p(C_out.data_ptr()), ldc, C.c_void_p(s.cuda_stream)))
+
+
+DEFAULT_CONFIG = dict(members=5, hidden=256, batch=256, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
+                      seed=1, log_inputs=0b0000110, log_outputs=0b0101,
+                      out_weight=(1.0, 1.0, 1.0, 0.25))
+
+
+class Surrogate:
+    """One ensemble (sg_handle)."""
+
+    def __init__(self, stream=None, **cfg):
+        import torch
+        c = dict(DEFAULT_CONFIG, **cfg)
+        conf = sg_config(c["members"], c["hidden"], c["batch"], c["lr"], c["beta1"], c["beta2"],
+                         c["eps"], c["seed"], c["log_inputs"], c["log_outputs"],
+                         (C.c_float * 4)(*c["out_weight"]))
+        self.config = c
+        s = torch.cuda.current_stream() if stream is None else stream
+        raw = s.cuda_stream
+        dev = torch.cuda.current_device()
+
+        def alloc(size, ctx):
+            return torch.cuda.caching_allocator_alloc(size, dev, raw)
+
+        def free(ptr, ctx):
+            torch.cuda.caching_allocator_delete(ptr)
+
+        self._cbs = (ij.ALLOC_FN(alloc), ij.FREE_FN(free))
+        out = C.c_void_p()
+        _check(_lib.sg_create(C.byref(conf), self._cbs[0], self._cbs[1], None, C.c_void_p(raw),
+                              C.byref(out)))
+        self.ptr = out
+
+    def __del__(self):
+        if getattr(self, "ptr", None) is not None and self.ptr.value:
+            _lib.sg_destroy(self.ptr)
+            self.ptr = C.c_void_p(None)
+
+    @property
+    def members(self):
+        return self.config["members"]
+
+    def set_data(self, x, y):
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        y = np.ascontiguousarray(y, dtype=np.float32)
+        assert x.shape[1] == N_IN and y.shape == (x.shape[0], N_OUT)
+        _check(_lib.sg_set_data(self.ptr, _ptr(x), _ptr(y), x.shape[0]))
+
+    def train(self, steps):
+        loss = C.c_double()
+        _check(_lib.sg_train(self.ptr, int(steps), C.byref(loss)))
+        return loss.value
+
+    def predict(self, x, gate=True):
+        """Ensemble mean [n][4], spread [n][4] and (gate) accept [n] of raw inputs."""
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        n = x.shape[0]
+        mean = np.empty((n, N_OUT), np.float32)
+        sd = np.empty((n, N_OUT), np.float32)
+        acc = np.empty(n, np.int32) if gate else None
+        _check(_lib.sg_predict(self.ptr, _ptr(x), n, _ptr(mean), _ptr(sd),
+                               _ptr(acc) if gate else None, 0))
+        return mean, sd, acc
+
+    def set_gate(self, tau, tau_v=None, nn_cut=0.0):
+        """Relative ensemble spread allowed on breakup time (tau) and droplet
+        velocity (tau_v, default tau); nn_cut <= 0 keeps the data's cut."""
+        tv = tau if tau_v is None else tau_v
+        _check(_lib.sg_set_gate(self.ptr, float(tau), float(tv), float(nn_cut)))
+
+    def param_count(self):
+        n = C.c_longlong()
+        _check(_lib.sg_param_count(self.ptr, C.byref(n)))
+        return n.value
+
+    def get_params(self, member):
+        out = np.empty(self.param_count(), np.float32)
+        _check(_lib.sg_get_params(self.ptr, member, _ptr(out)))
+        return out
+
+    def set_params(self, member, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == self.param_count()
+        _check(_lib.sg_set_params(self.ptr, member, _ptr(p)))
+
+    def transform(self):
+        a, b = np.empty(N_IN, np.float32), np.empty(N_IN, np.float32)
+        c, d = np.empty(N_OUT, np.float32), np.empty(N_OUT, np.float32)
+        _check(_lib.sg_get_transform(self.ptr, _ptr(a), _ptr(b), _ptr(c), _ptr(d)))
+        return a, b, c, d
+
+    def gradients(self, x, y):
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        y = np.ascontiguousarray(y, dtype=np.float32)
+        g = np.empty((self.members, self.param_count()), np.float32)
+        loss = np.empty(self.members, np.float64)
+        _check(_lib.sg_gradients(self.ptr, _ptr(x), _ptr(y), x.shape[0], _ptr(g), _ptr(loss)))
+        return g, loss
+
+
+def unpack(p, hidden):
+    """Member parameter vector -> lists Wt [out][in] and b [out] per layer."""
+    nin = (16, hidden, hidden, hidden, hidden)
+    nout = (hidden, hidden, hidden, hidden, 16)
+    Wt, b, off = [], [], 0
+    for i, o in zip(nin, nout):
+        Wt.append(p[off:off + i * o].reshape(o, i))
+        off += i * o
+        b.append(p[off:off + o])
+        off += o
+    return Wt, b
+
+
+# ---------------------------------------------------------------------------
+# Inputs, lattices and outcomes.
+
+# A regime where the planar nozzle ejects one droplet within ~2000-4500
+# steps for most draws: ejection needs nozzles of 17 lattice units and more
+# and a drive of about 2e-3 and above at these surface tensions (narrower
+# nozzles and weaker drives only bulge the meniscus; much stronger drives
+# and wider nozzles push a column through the top of the domain instead).
+INPUT_BOX = dict(theta_deg=(30.0, 150.0), sigma=(0.0012, 0.002), F0=(2.1e-3, 2.5e-3),
+                 T1=(1000, 1200), T2=(900, 1200), T_idle=(2000, 4000), width=(17, 19))
+
+
+def sample_inputs(n, seed):
+    """n rows of the seven inputs, uniform over INPUT_BOX (sigma and F0
+    log-uniform, durations and width integers)."""
+    rng = np.random.default_rng(seed)
+    b = INPUT_BOX
+    x = np.empty((n, N_IN))
+    x[:, 0] = rng.uniform(*b["theta_deg"], n)
+    x[:, 1] = np.exp(rng.uniform(np.log(b["sigma"][0]), np.log(b["sigma"][1]), n))
+    x[:, 2] = np.exp(rng.uniform(np.log(b["F0"][0]), np.log(b["F0"][1]), n))
+    x[:, 3] = rng.integers(b["T1"][0], b["T1"][1] + 1, n)
+    x[:, 4] = rng.integers(b["T2"][0], b["T2"][1] + 1, n)
+    x[:, 5] = rng.integers(b["T_idle"][0], b["T_idle"][1] + 1, n)
+    x[:, 6] = rng.integers(b["width"][0], b["width"][1] + 1, n)
+    return x
+
+
+def lattice_params(row, seed=0):
+    theta, sigma, F0, T1, T2, T_idle, w = [float(v) for v in row]
+    w = int(round(w))
+    return dict(nx=4 * w, ny=24 * w, geometry=W.GEOM_NOZZLE, nozzle_width=w, nozzle_length=3 * w,
+                wall_thickness=4, rho_ink=10.0, rho_air=1.0, nu_ink=0.1, nu_air=0.05, sigma=sigma,
+                width_W=3.0, tau_phi=0.8, gamma=0.0, theta_deg=theta, F0=F0, F_neg=F0 / 2,
+                T1=int(T1), T2=int(T2), T_idle=int(T_idle), axial_bc=W.BC_ZERO_GRADIENT,
+                init_kind=W.INIT_MENISCUS, jitter=1e-6, seed=seed, diag_every=10)
+
+
+def outcomes_from_history(hist, after=(0, 100)):
+    """Breakup time, and droplet velocity, volume and satellites averaged
+    over the records from breakup + after[0] to breakup + after[1] (the
+    droplet just after pinch-off, before the weak drive lets it slow down).
+    NaN row when no breakup happened early enough to fill the window."""
+    tb = hist[-1, 5]
+    if tb <= 0 or hist[-1, 0] < tb + after[1]:
+        return np.full(N_OUT, np.nan)
+    sel = (hist[:, 0] >= tb + after[0]) & (hist[:, 0] <= tb + after[1])
+    return np.array([tb, hist[sel, 8].mean(), hist[sel, 6].mean(), hist[sel, 9].mean()])
+
+
+def lbm_outcomes(rows, steps=5000, stream=None, chunk=1024):
+    """Run every input row as a lattice of the batched LBM path for `steps`
+    steps; returns outcomes [n][4] (NaN rows: no breakup in time)."""
+    out = np.empty((len(rows), N_OUT))
+    for a in range(0, len(rows), chunk):
+        part = rows[a:a + chunk]
+        h = ij.ij_create([lattice_params(r, seed=a + k) for k, r in enumerate(part)], stream=stream)
+        ij.ij_step(h, steps)
+        for k in range(len(part)):
+            out[a + k] = outcomes_from_history(ij.ij_history(h, k))
+        ij.ij_destroy(h)
+    return out
+
+
+class SurrogateService:
+    """Answers queries with the ensemble where the gate accepts them and
+    with the lattice Boltzmann model elsewhere."""
+
+    def __init__(self, surrogate, lbm_steps=5000):
+        self.sg = surrogate
+        self.lbm_steps = lbm_steps
+
+    def query(self, x):
+        mean, sd, acc = self.sg.predict(x, gate=True)
+        out = mean.astype(np.float64)
+        rej = np.nonzero(acc == 0)[0]
+        if len(rej):
+            out[rej] = lbm_outcomes(x[rej], steps=self.lbm_steps)
+        return out, acc.astype(bool)
+
+
+def relative_error(pred, ref):
+    return np.abs(pred - ref) / np.maximum(np.abs(ref), 1e-30)
+
+
+def finite_rows(y):
+    return np.all(np.isfinite(y), axis=1)
+
+
+def describe_inputs():
+    return {k: INPUT_BOX[k] for k in INPUT_NAMES}
+
+
+__all__ = ["Surrogate", "SurrogateService", "sample_inputs", "lattice_params", "lbm_outcomes",
+           "outcomes_from_history", "gemm_bf16", "unpack", "relative_error", "finite_rows",
+           "describe_inputs", "INPUT_BOX"]

@@ -63,3 +63,28 @@ def test_binding_and_oracle_share_only_the_parameter_names():
     orc_fields = [f[0] for f in _Params._fields_]
     assert set(orc_fields) <= set(lib_fields)
     assert set(lib_fields) - set(orc_fields) == {"precision", "dim"}
+
+
+def test_library_exports_every_surrogate_symbol():
+    import os
+    import re
+    with open(os.path.join(os.path.dirname(inkjet.HEADER), "surrogate.h")) as fh:
+        names = sorted(set(re.findall(r"\b(sg_[a-z_0-9]+)\s*\(", fh.read())))
+    assert "sg_create" in names and "sg_train" in names and "sg_gemm_bf16" in names
+    lib = C.CDLL(inkjet.library_path())
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_surrogate_config_is_checked_on_the_host():
+    from paper_1702_04487_gb300 import surrogate as S
+    for bad in (dict(members=0), dict(members=9), dict(hidden=20), dict(hidden=512),
+                dict(batch=8), dict(lr=0.0), dict(beta1=1.0)):
+        c = dict(S.DEFAULT_CONFIG, **bad)
+        conf = S.sg_config(c["members"], c["hidden"], c["batch"], c["lr"], c["beta1"], c["beta2"],
+                           c["eps"], c["seed"], c["log_inputs"], c["log_outputs"],
+                           (C.c_float * 4)(*c["out_weight"]))
+        out = C.c_void_p(7)
+        st = S._lib.sg_create(C.byref(conf), inkjet.ALLOC_FN(), inkjet.FREE_FN(), None, None,
+                              C.byref(out))
+        assert st == inkjet.IJ_ERR_PARAM and out.value is None
