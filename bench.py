@@ -227,7 +227,12 @@ def run_native(args):
 
     # ---- device-resident throughput
     h = inkjet.ij_create(params)
-    tuning = inkjet.ij_autotune(h, 3) if args.autotune else inkjet.ij_get_tuning(h)
+    if args.tune:
+        chunk, pf = (int(v) for v in args.tune.split(","))
+        inkjet.ij_tune(h, 0, chunk, pf)
+        tuning = inkjet.ij_get_tuning(h)
+    else:
+        tuning = inkjet.ij_autotune(h, 3) if args.autotune else inkjet.ij_get_tuning(h)
     inkjet.ij_step(h, args.warmup)
     barrier()
     clocks = ClockSampler(local)
@@ -434,6 +439,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the default launch shape instead of timing candidates first")
+    ap.add_argument("--tune", default="",
+                    help="CHUNK,PREFETCH: fixed launch shape of the 2-D step instead of autotuning")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--surrogate", action="store_true",
                     help="measure the surrogate sweep (data generation, training, gated queries)")

@@ -198,18 +198,19 @@ ij_status ij_launch_count(ij_handle h, long long* launches);
 ij_status ij_kernel_timing(ij_handle h, int enable, double* total_ms, long long* launches);
 
 /*
- * Launch-shape tuning (no counterpart in the paper).  Lattices of a handle
- * are launched in buckets of equal block size (one thread per column, up to
- * 256; wider lattices use overlapping 256-column strips).  Each bucket splits
- * its lattices' rows into chunks of `chunk` rows (one block per strip and
- * chunk) and stages populations `prefetch` rows (1 or 2) ahead of use.
+ * Launch-shape tuning (no counterpart in the paper).  The step kernel runs
+ * one warp per work item: a strip of 28 columns (plus two halo columns on
+ * each side) times a chunk of `chunk` rows of one lattice, with the
+ * populations staged `prefetch` rows (1..4) ahead of use; blocks of 128
+ * threads carry four items.  Every lattice of a handle is in the one bucket
+ * of 128-thread blocks.
  *
- * ij_tune      -- set chunk and prefetch for the bucket of `block_size`
- *                 threads (block_size <= 0: every bucket).  Synchronises.
+ * ij_tune      -- set chunk and prefetch (block_size: 128, or <= 0 for
+ *                 every bucket).  Synchronises.
  * ij_autotune  -- time `reps` trial launches of every candidate (chunks
- *                 8..192, prefetch 1..2) per bucket on the current state and
- *                 keep the fastest.  Trial launches leave the state and the
- *                 time unchanged.  Synchronises.
+ *                 16..256, prefetch 1..4) on the current state and keep the
+ *                 fastest.  Trial launches leave the state and the time
+ *                 unchanged.  Synchronises.
  * ij_get_tuning -- block size, chunk, prefetch and item count of bucket
  *                 `bucket` (0-based); IJ_ERR_PARAM past the last bucket.
  * 3-D handles have one fixed launch shape and no buckets: ij_tune returns
@@ -248,9 +249,9 @@ ij_status ij_get_tuning(ij_handle h, int bucket, int* block_size, int* chunk, in
  *                   Each call starts a fresh breakup history, so breakup_step
  *                   is t when the neck is already closed, else -1.
  *   stream        : cudaStream_t to enqueue on; the call is asynchronous.
- * Limits: ny <= 8192 and at most 4096 work items (strips of 254 columns times
- * chunks of 32 rows); larger lattices are rejected with IJ_ERR_PARAM.
- * Descriptors and scratch live in one fixed device array of about 0.3 MB per
+ * Limits: ny <= 8192 and at most 16384 work items (strips of 28 columns times
+ * chunks of 64 rows); larger lattices are rejected with IJ_ERR_PARAM.
+ * Descriptors and scratch live in one fixed device array of about 0.6 MB per
  * GPU that loads the library, kept until the process exits.  The first call
  * on a device looks up that array's device address, so make it before any
  * stream capture.  Every call shares the array: calls whose GPU work

@@ -309,50 +309,32 @@ Inst3 derive3(const ij_params& p) {
 
 // Block size of a lattice: one strip of round_up(nx, 32) threads when nx
 // fits in 256 columns, else overlapping strips of 256 threads.
-int block_size_for(const Inst& I) { return I.nx <= 256 ? (I.nx + 31) / 32 * 32 : 256; }
+// Every lattice runs in the one bucket of kStepThreads-thread blocks (one
+// warp per work item).
+int block_size_for(const Inst&) { return kStepThreads; }
 
-// Items of one lattice: strips of columns x chunks of rows.
-void lattice_items(const Inst& I, int k, int chunk, std::vector<Item>& out) {
-  const int nt = block_size_for(I);
-  const int single = I.nx <= 256;
-  const int wc = single ? I.nx : nt, stride = single ? 0 : nt - 2;
-  const int nstrip = single ? 1 : (I.nx + stride - 1) / stride;
-  for (int s = 0; s < nstrip; s++)
-    for (int y0 = 0; y0 < I.ny; y0 += chunk) {
-      Item it;
-      it.inst = k;
-      it.xs = single ? 0 : s * stride - 1;
-      it.wc = wc;
-      it.single = single;
-      it.y0 = y0;
-      it.ch = std::min(chunk, I.ny - y0);
-      out.push_back(it);
-    }
-}
-
-// Work list grouped by block size; each bucket keeps its chunk and prefetch
-// (defaults: 32 rows, the deepest prefetch that keeps two blocks per SM).
 void build_items(ij_handle h) {
-  std::vector<int> sizes;
-  for (int k = 0; k < h->n_inst; k++) sizes.push_back(block_size_for(h->inst[k]));
-  std::sort(sizes.begin(), sizes.end());
-  sizes.erase(std::unique(sizes.begin(), sizes.end()), sizes.end());
   std::vector<Bucket> old = h->buckets;
   h->items.clear();
   h->buckets.clear();
-  for (int nt : sizes) {
-    Bucket b{nt, (int)h->items.size(), 0, 0, 32, step_prefetch_for(nt)};
-    for (const Bucket& o : old)
-      if (o.nthreads == nt) {
-        b.chunk = o.chunk;
-        b.prefetch = o.prefetch;
-      }
-    for (int k = 0; k < h->n_inst; k++)
-      if (block_size_for(h->inst[k]) == nt) lattice_items(h->inst[k], k, b.chunk, h->items);
-    b.count = (int)h->items.size() - b.first;
-    b.grid = b.count;
-    h->buckets.push_back(b);
+  Bucket b{kStepThreads, 0, 0, 0, 64, step_prefetch_for(kStepThreads)};
+  for (const Bucket& o : old)
+    if (o.nthreads == kStepThreads) {
+      b.chunk = o.chunk;
+      b.prefetch = o.prefetch;
+    }
+  for (int k = 0; k < h->n_inst; k++) {
+    const int n = items_per_lattice(h->inst[k], b.chunk);
+    const size_t at = h->items.size();
+    h->items.resize(at + n);
+    make_items(h->inst[k], k, b.chunk, h->items.data() + at, n);
   }
+  b.count = (int)h->items.size();
+  // one block per four items: the block scheduler hands new blocks to SMs
+  // as they free up (measured faster than a persistent grid walking the
+  // list with a stride)
+  b.grid = (b.count + kStepThreads / 32 - 1) / (kStepThreads / 32);
+  h->buckets.push_back(b);
 }
 
 // Upload the work list, growing the device copy when needed (the captured
@@ -643,6 +625,7 @@ ij_status ij_create(const ij_params* params, int count, ij_alloc_fn alloc, ij_fr
   h->n_inst = count;
   h->params.assign(params, params + count);
   h->stream = (cudaStream_t)stream;
+
   h->alloc = alloc;
   h->free_fn = free_fn;
   h->ctx = ctx;
@@ -918,14 +901,11 @@ ij_status ij_tune(ij_handle h, int block_size, int chunk, int prefetch) {
   ij_status st = check_handle(h);
   if (st != IJ_OK) return st;
   if (h->is3d) return fail(IJ_ERR_PARAM, "3-D handles have no launch shape to tune");
-  if (chunk < 1 || (prefetch != 1 && prefetch != 2))
-    return fail(IJ_ERR_PARAM, "chunk must be >= 1 and prefetch 1 or 2");
+  if (chunk < 1 || prefetch < 1 || prefetch > kMaxPrefetch)
+    return fail(IJ_ERR_PARAM, "chunk must be >= 1 and prefetch in 1..%d", kMaxPrefetch);
   bool found = false;
   for (Bucket& b : h->buckets)
     if (block_size <= 0 || b.nthreads == block_size) {
-      if (prefetch > step_prefetch_for(b.nthreads))
-        return fail(IJ_ERR_PARAM, "prefetch %d does not fit two blocks of %d threads per SM",
-                    prefetch, b.nthreads);
       found = true;
     }
   for (Bucket& b : h->buckets)
@@ -945,7 +925,7 @@ ij_status ij_autotune(ij_handle h, int reps) {
   if (reps < 1) return fail(IJ_ERR_PARAM, "reps must be >= 1");
   if (h->poisoned) return fail(IJ_ERR_STATE, "handle is poisoned");
   if (h->is3d) return IJ_OK;  // the 3-D kernels have one fixed launch shape
-  static const int kChunks[] = {8, 16, 24, 32, 48, 64, 96, 128, 192};
+  static const int kChunks[] = {16, 32, 48, 64, 96, 128, 192, 256};
   cudaEvent_t e0, e1;
   CUDA_TRY(cudaEventCreate(&e0));
   CUDA_TRY(cudaEventCreate(&e1));
@@ -958,7 +938,7 @@ ij_status ij_autotune(ij_handle h, int reps) {
       if (block_size_for(h->inst[k]) == nt) max_ny = std::max(max_ny, h->inst[k].ny);
     float best = 1e30f;
     int best_chunk = h->buckets[bi].chunk, best_pf = h->buckets[bi].prefetch;
-    for (int pf = 1; pf <= step_prefetch_for(nt); pf++)
+    for (int pf = 1; pf <= kMaxPrefetch; pf++)
       for (int chunk : kChunks) {
         if (chunk > 2 * max_ny && chunk != kChunks[0]) continue;
         h->buckets[bi].chunk = chunk;

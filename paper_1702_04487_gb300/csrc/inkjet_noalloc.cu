@@ -13,7 +13,7 @@
 //
 // The array below is sized for one lattice of at most kMaxRows rows and
 // kMaxItems work items; every GPU that loads the library holds it (about
-// 0.3 MB) until the process exits.  All calls on a device share it and it
+// 0.6 MB) until the process exits.  All calls on a device share it and it
 // keeps the last call's contents, so each call clears the parts that must
 // start at zero, and calls whose GPU work overlaps (for example on two
 // streams) race on it.
@@ -30,8 +30,8 @@ namespace {
 using namespace ij;
 
 constexpr int kMaxRows = 8192;
-constexpr int kMaxItems = 4096;
-constexpr int kChunk = 32;  // rows per work item, as in ij_create
+constexpr int kMaxItems = 16384;
+constexpr int kChunk = 64;  // rows per work item, as in ij_create
 constexpr int kMaxDevices = 64;
 
 constexpr size_t a256(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -89,39 +89,14 @@ extern "C" ij_status ij_step_noalloc(const ij_params* params, long long t, const
   if (p.ny > kMaxRows)
     return report(IJ_ERR_PARAM, "ij_step_noalloc: ny exceeds the fixed scratch limit of 8192 rows");
   // work list: the same strips and row chunks ij_create builds for one lattice
-  int nt, wc, single, stride, nstrip;
-  if (p.nx <= 256) {
-    nt = (p.nx + 31) / 32 * 32;
-    wc = p.nx;
-    single = 1;
-    stride = 0;
-    nstrip = 1;
-  } else {
-    nt = 256;
-    wc = nt;
-    single = 0;
-    stride = nt - 2;
-    nstrip = (p.nx + stride - 1) / stride;
-  }
-  const long long n_items = (long long)nstrip * ((p.ny + kChunk - 1) / kChunk);
-  if (n_items > kMaxItems)
-    return report(IJ_ERR_PARAM, "ij_step_noalloc: lattice needs more than the fixed 4096 work items");
-  int k = 0;
-  for (int s = 0; s < nstrip; s++)
-    for (int y0 = 0; y0 < p.ny; y0 += kChunk) {
-      Item& it = t_items[k++];
-      it.inst = 0;
-      it.xs = single ? 0 : s * stride - 1;
-      it.wc = wc;
-      it.single = single;
-      it.y0 = y0;
-      it.ch = p.ny - y0 < kChunk ? p.ny - y0 : kChunk;
-    }
+  Inst I = derive_params(p);
+  const int n_items = make_items(I, 0, kChunk, t_items, kMaxItems);
+  if (n_items < 0)
+    return report(IJ_ERR_PARAM, "ij_step_noalloc: lattice needs more than the fixed 16384 work items");
   unsigned char* base = nullptr;
   st = scratch_base(&base);
   if (st != IJ_OK) return st;
 
-  Inst I = derive_params(p);
   I.f[t & 1] = const_cast<float*>(f_in);
   I.g[t & 1] = const_cast<float*>(g_in);
   I.f[(t + 1) & 1] = f_out;
@@ -154,8 +129,9 @@ extern "C" ij_status ij_step_noalloc(const ij_params* params, long long t, const
     NOALLOC_TRY(cudaMemsetAsync(base + kOffSums, 0, 4 * sizeof(double), s));
     NOALLOC_TRY(cudaMemcpyAsync(base + kOffDstate, dinit, sizeof(dinit), cudaMemcpyHostToDevice, s));
   }
-  NOALLOC_TRY(launch_step(d_inst, d_items, (int)n_items, nt, (int)n_items, d_t, 0, diag,
-                          step_prefetch_for(nt), s));
+  NOALLOC_TRY(launch_step(d_inst, d_items, n_items, kStepThreads,
+                          (n_items + kStepThreads / 32 - 1) / (kStepThreads / 32), d_t, 0, diag,
+                          step_prefetch_for(kStepThreads), s));
   if (diag) {
     NOALLOC_TRY(launch_finalize(d_inst, 1, d_t, s));
     NOALLOC_TRY(cudaMemcpyAsync(record_out, base + kOffHist, kRec * sizeof(double),

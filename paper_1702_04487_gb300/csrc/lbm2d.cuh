@@ -14,7 +14,6 @@ enum { INIT_MENISCUS = 0, INIT_DROP = 1, INIT_FLAT = 2, INIT_UNIFORM = 3 };
 
 constexpr int kRec = 12;        // doubles per diagnostics record
 constexpr int kHistCap = 1024;  // records kept per lattice (ring)
-constexpr int kMaxThreads = 256;
 constexpr unsigned kStatusNumeric = 1u;
 
 // One lattice.  FP32 constants feed the step kernel; FP64 ones the
@@ -43,15 +42,23 @@ struct Inst {
   unsigned* status;  // this lattice's numeric flag (NaN or |u| > 0.3 seen)
 };
 
-// A unit of work of the step kernel: `ch` rows starting at y0 of a strip of
-// `wc` collision columns starting at column xs (wrapped) of lattice `inst`.
-// single != 0: the strip is the whole periodic width (wc == nx).
+// A unit of work of the step kernel (one warp): `ch` rows starting at y0 of
+// the strip of lattice `inst` that writes columns xs .. xs + nout - 1; lane l
+// holds column xs - halo + l (periodic wrap).
 struct Item {
-  int inst, xs, wc, single, y0, ch;
+  int inst, xs, nout, halo, y0, ch;
 };
+
+constexpr int kStepThreads = 128;  // 4 warps per block, one work item each
+constexpr int kStepBlocksPerSM = 4;  // resident blocks per SM (registers)
+constexpr int kMaxPrefetch = 4;    // rows staged ahead of use: 1 .. 4
 
 size_t step_smem_bytes(int nthreads, int prefetch);
 cudaError_t set_step_smem_limit();
+// Work items of one lattice (row chunks of `chunk` rows x strips) into out
+// (at most cap); returns the count, or -1 when cap is too small.
+int make_items(const Inst& I, int k, int chunk, Item* out, int cap);
+int items_per_lattice(const Inst& I, int chunk);
 
 // host helpers of inkjet_api.cu
 ij_status validate_params(const ij_params& p, int k);
@@ -62,8 +69,7 @@ cudaError_t launch_init(const Inst* d_inst, const Inst& h_inst, int index, cudaS
 cudaError_t launch_step(const Inst* d_inst, const Item* d_items, int n_items, int nthreads,
                         int grid, const long long* d_t, int t_off, bool diag, int prefetch,
                         cudaStream_t s);
-// rows staged ahead of use (1 or 2): 2 when two blocks of nthreads still fit
-// one SM's shared memory, else 1
+// default number of rows staged ahead of use
 int step_prefetch_for(int nthreads);
 cudaError_t launch_finalize(const Inst* d_inst, int n_inst, const long long* d_t,
                             cudaStream_t s);

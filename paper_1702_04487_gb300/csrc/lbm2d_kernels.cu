@@ -55,6 +55,37 @@ __device__ __forceinline__ bool map_row(const Inst& I, int y, int& ym) {
   return false;
 }
 
+// The same mapping and near-solid test from values held in registers.
+__device__ __forceinline__ bool map_row_v(int y, int ny, int bc, int& ym) {
+  if ((unsigned)y < (unsigned)ny) {
+    ym = y;
+    return true;
+  }
+  if (bc == BC_PER) {
+    ym = wrapi(y, ny);
+    return true;
+  }
+  if (bc == BC_ZG) {
+    ym = y < 0 ? 0 : ny - 1;
+    return true;
+  }
+  return false;
+}
+__device__ __forceinline__ bool near_solid_v(int geom, int bc, int ny, int L, int wt, bool colwall,
+                                             int y) {
+  if (bc == BC_CLOSED && (y == 0 || y == ny - 1)) return true;
+  if (geom == GEOM_NOZZLE) {
+    if (!colwall) return false;
+    if (bc == BC_PER && (y == 0 || y == ny - 1)) return true;
+    return y - 1 < L;
+  }
+  if (geom == GEOM_PLATE) {
+    if (bc == BC_PER && (y == 0 || y == ny - 1)) return true;
+    return y - 1 < wt;
+  }
+  return false;
+}
+
 // Kind of an in-domain cell: 0 fluid, 1 solid, 2 solid on a wetting face.
 __device__ __forceinline__ int geom_kind(const Inst& I, int x, int y) {
   if (I.geom == GEOM_NOZZLE) {
@@ -104,34 +135,19 @@ __device__ __forceinline__ float drive_at(const Inst& I, long long t) {
   return 0.0f;
 }
 
-// Wetting ghost value of a solid point from a 3x3 window of phi (centre
-// w[4], rows w[0..2] below, w[6..8] above) and the kinds of its neighbours:
-// the mean over fluid face neighbours of phi + h_s / kappa, else the mean
-// over fluid diagonal neighbours.
-__device__ __noinline__ float ghost_rule(const Inst& I, int kind, int x, int y, const float* w) {
-  float hk = (kind == 2) ? I.hk : 0.0f;
-  const int fx[4] = {1, 0, -1, 0}, fy[4] = {0, 1, 0, -1};
-  float sum = 0.0f;
-  int cnt = 0;
-  for (int d = 0; d < 4; d++)
-    if (kind_at(I, x + fx[d], y + fy[d]) == 0) {
-      sum += w[(fy[d] + 1) * 3 + fx[d] + 1] + hk;
-      cnt++;
-    }
-  if (cnt) return sum / (float)cnt;
-  const int dx[4] = {1, -1, -1, 1}, dy[4] = {1, 1, -1, -1};
-  for (int d = 0; d < 4; d++)
-    if (kind_at(I, x + dx[d], y + dy[d]) == 0) {
-      sum += w[(dy[d] + 1) * 3 + dx[d] + 1];
-      cnt++;
-    }
-  return cnt ? sum / (float)cnt : 0.0f;
-}
-
 // Asynchronous 4-byte global -> shared copies (cp.async), grouped per row.
 __device__ __forceinline__ void cp_async4(float* dst, const float* src) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(src) : "memory");
+}
+// The same copy issued only when pred is set (a predicated instruction, no
+// branch).
+__device__ __forceinline__ void cp_async4_if(float* dst, const float* src, bool pred) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %2, 0;\n @p cp.async.ca.shared.global [%0], [%1], 4;\n}\n" ::"r"(sa),
+      "l"(src), "r"((int)pred)
+      : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() {
   asm volatile("cp.async.commit_group;\n" ::: "memory");
@@ -171,427 +187,376 @@ __device__ __forceinline__ int column_kind(const Inst& I, int x) {
 }
 
 // ---------------------------------------------------------------------------
-// The fused step.  Shared memory per block (NT = blockDim.x, D = P + 3):
-//   ring[D] rows of populations staged by cp.async, P rows ahead of use:
-//           g[5][NT+4] (slot j <-> column xs+j-2) and f[9][NT] (slot c <-> xs+c)
-//   raw[4][NT+4]  phi of rows R..R-3 (ring), slot j <-> column xs+j-2
-//   gh [3][NT+2]  phi with ghost values, slot j <-> column xs+j-1
-//   col[3][12][NT] post-collision f_1..8 and moving g parts P_1..4
-//   red[NT/32][3] diagnostics partial sums (FP64)
+// The fused step: one warp per work item (a strip of columns x a chunk of
+// rows of one lattice); warps never wait on one another.
+//
+// Lane l of a strip holds column x = xs - 2 + l (periodic wrap).  The strip
+// writes the nout <= 28 columns of lanes 2 .. nout+1; lanes 1 and nout+2
+// collide too (the streaming pulls their post-collision populations), and
+// lanes 0 and 31 only contribute phi to the stencil.  When lane 0 or 31
+// sits on a wall, its ghost value needs phi beyond the strip: that lane
+// stages the g of the column outside as well.  Neighbours along x are
+// exchanged with warp shuffles; along y each lane keeps its own column's
+// last rows in registers while the warp marches up the rows.
+//
+// Per row iteration (pipeline row R): phi of row R (sum of g); the wetting
+// ghost values of row R-1 (only rows with a solid cell in the strip); the
+// collision of row R-2 (Eq. 4-6 for f, Eq. 8-10 for g); the streaming of
+// row R-3 with halfway bounce-back and the stay/move split of Eq. 8, stored
+// to the other time buffer.  Every lane stages its own column's 14
+// populations of row R+P into the warp's shared-memory ring with cp.async,
+// P rows ahead of use, and reads back only what it staged itself.
+constexpr int kWarpsPerBlock = 4;
+constexpr int kRowFloats = 14 * 32;  // one staged row of a warp: g[5][32], then f[9][32]
+constexpr unsigned kFull = 0xffffffffu;
+
 template <bool DIAG, int P>
-__global__ void __launch_bounds__(256, 2) step_kernel(const Inst* __restrict__ insts,
-                                                      const Item* __restrict__ items, int n_items,
-                                                      const long long* __restrict__ d_t, int t_off) {
-  constexpr int D = P + 3;
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, kStepBlocksPerSM)
+    step_kernel(const Inst* __restrict__ insts, const Item* __restrict__ items, int n_items,
+                const long long* __restrict__ d_t, int t_off) {
+  constexpr int D = P + 3;  // ring rows: R+P .. R-2 are live
   extern __shared__ float4 smem4[];
-  float* smem = reinterpret_cast<float*>(smem4);
-  const int NT = blockDim.x;
-  const int c = threadIdx.x;
-  const int GW = NT + 4, RS = 5 * GW + 9 * NT;  // g row width, ring slot size (floats)
-  float* ring = smem;
-  float* raw = ring + D * RS;
-  float* gh = raw + 4 * (NT + 4);
-  float* col = gh + 3 * (NT + 2);
-  double* red = reinterpret_cast<double*>(col + 36 * NT);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float* ring = reinterpret_cast<float*>(smem4) + warp * D * kRowFloats + lane;
   const long long t = *d_t + t_off;
 
-  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+  for (int item = blockIdx.x * kWarpsPerBlock + warp; item < n_items;
+       item += gridDim.x * kWarpsPerBlock) {
     const Item it = items[item];
     const Inst& I = insts[it.inst];
-    // a lattice whose numeric flag is set is frozen; thread 0 reads the flag
-    // and the barrier-reduction makes the decision uniform across the block
-    if (__syncthreads_or(c == 0 ? (int)*(volatile unsigned*)I.status : 0)) continue;
-    // per-lattice constants in registers
+    // a lattice whose numeric flag is set is frozen
+    const unsigned st0 = lane == 0 ? *(volatile const unsigned*)I.status : 0u;
+    if (__shfl_sync(kFull, st0, 0) & kStatusNumeric) continue;
     const int nx = I.nx, ny = I.ny, geom = I.geom, L = I.L, wt = I.wt, bc = I.bc;
-    const int wc = it.wc, y0 = it.y0, ch = it.ch;
     const int N = nx * ny;  // < 2^31 / 9 (checked on the host)
-#define phis2 (I.phis * I.phis)
-#define inv_phis (I.inv_phis)
-#define A4 (I.A4)
-#define kappa (I.kappa)
-#define qf (I.q)
-#define omq (I.omq)
-#define inv_tphi (I.inv_tphi)
-#define gamma (I.gamma)
-#define inv2q (I.inv2q)
-#define nu_air (I.nu_air)
-#define dnu (I.dnu)
-#define n0 (I.n0)
+    const int y0 = it.y0, ch = it.ch;
+    const int x = wrapi(it.xs - it.halo + lane, nx);
+    const bool out_lane = lane >= it.halo && lane < it.halo + it.nout;
+    const bool col_lane = lane >= it.halo - 1 && lane <= it.halo + it.nout;
+    const int ck = column_kind(I, x);
+    const int ckW = column_kind(I, wrapi(x - 1, nx)), ckE = column_kind(I, wrapi(x + 1, nx));
+    const bool colwall = geom == GEOM_NOZZLE && (ck | ckW | ckE) != 0;
+    // lanes 0 and 31 on a wall column: the column outside the strip (xo)
+    const bool edge = (lane == 0 || lane == 31) && ck != 0;
+    const int xo = wrapi(lane == 0 ? x - 1 : x + 1, nx);
+    const int cko = lane == 0 ? ckW : ckE;
+    const bool drive_col = geom != GEOM_NOZZLE || (x >= I.cx0 && x < I.cx1);
+    const float phis = I.phis, inv_phis = I.inv_phis, A4 = I.A4, kappa = I.kappa, hk = I.hk;
+    const float qf = I.q, omq = I.omq, inv_tphi = I.inv_tphi, gamma = I.gamma, inv2q = I.inv2q;
+    const float nu_air = I.nu_air, dnu = I.dnu, n0 = I.n0;
+    const float Fd = drive_at(I, t);
     const float* __restrict__ fin = I.f[t & 1];
     const float* __restrict__ gin = I.g[t & 1];
     float* __restrict__ fout = I.f[(t + 1) & 1];
     float* __restrict__ gout = I.g[(t + 1) & 1];
-    const float Fd = drive_at(I, t);
-    const bool active = c < wc;
-    const int x = wrapi(it.xs + c, nx);
-    const bool owned = active && (it.single || (c >= 1 && c <= wc - 2 && it.xs + c < nx));
-    const int xe = (c < 2) ? c : wc + c;  // extra raw slot of threads 0..3
-    const int xex = wrapi(it.xs + xe - 2, nx);
-    const int xg = (c == 0) ? 0 : wc + 1;  // extra ghost slot of threads 0..1
-    const int xgx = wrapi(it.xs + xg - 1, nx);
-    const int ck = column_kind(I, x), cke = column_kind(I, xex), ckg = column_kind(I, xgx);
-    const bool drive_col = geom != GEOM_NOZZLE || (x >= I.cx0 && x < I.cx1);
-    // does the strip (with its halo) contain a nozzle-wall column?  Rows with
-    // no solid cell in the strip need no ghost values: their phi is used as is
-    bool strip_wall = false;
-    if (geom == GEOM_NOZZLE) {
-      const int a0 = I.cx0 - I.wt, b1 = I.cx1 + I.wt;
-      if (it.single) {
-        strip_wall = true;
-      } else {
-        for (int j = -2; j < wc + 2 && !strip_wall; j++) {
-          const int xx = wrapi(it.xs + j, nx);
-          strip_wall = xx >= a0 && xx < b1 && column_kind(I, xx) != 0;
-        }
-      }
-    }
-    bool colwall = false;
-    if (geom == GEOM_NOZZLE)
-      colwall = ck != 0 || column_kind(I, wrapi(x - 1, nx)) != 0 ||
-                column_kind(I, wrapi(x + 1, nx)) != 0;
 
-    // rotating per-row state of the own column: kinds of rows R..R-3, mapped
-    // rows of R..R-2
-    int k0 = 1, k1 = 1, k2 = 1, k3 = 1;
-    int m0 = 0, m1 = 0, m2 = 0;
-    // block-uniform: does pipeline row R, R-1, R-2, R-3 hold a solid cell?
-    bool h0 = true, h1 = true, h2 = true, h3 = true;
-    int keR = 1;  // kind of the extra raw column (threads 0..3) in row R
-    // Stage the populations of pipeline row r into ring slot `slot` (own
-    // column; the g halo columns by threads 0..3; f only for rows that are
-    // collided), as one cp.async group.
-    auto stage_row = [&](int r, int slot) {
+    // Stage pipeline row r into ring slot sp (own column; f only for rows
+    // that are collided), as one cp.async group.
+    auto stage = [&](int r, int sp) {
       int ym;
-      const bool in = r <= y0 + ch + 2 && map_row(I, r, ym);
-      if (in) {
-        float* sg = ring + slot * RS;
-        const int off = ym * nx;
-        if (active && row_kind(geom, ck, L, wt, ym) == 0) {
-          const float* q = gin + off + x;
+      if (r <= y0 + ch + 2 && map_row_v(r, ny, bc, ym)) {  // uniform over the warp
+        float* d = ring + sp * kRowFloats;
+        const bool own = row_kind(geom, ck, L, wt, ym) == 0;
+        const bool fneed = own && col_lane && r >= y0 - 1 && r <= y0 + ch;
+        // a solid edge lane has no populations of its own: the g of the
+        // column outside the strip go where its f would be
+        const bool outer = edge && !own && row_kind(geom, cko, L, wt, ym) == 0;
+        const float* qg = gin + (ym * nx + x);
+        const float* qf = outer ? gin + (ym * nx + xo) : fin + (ym * nx + x);
 #pragma unroll
-          for (int i = 0; i < 5; i++) cp_async4(sg + i * GW + c + 2, q + i * N);
-          if (r >= y0 - 1 && r <= y0 + ch) {
-            const float* qf_ = fin + off + x;
-            float* sf = sg + 5 * GW;
+        for (int i = 0; i < 5; i++) cp_async4_if(d + i * 32, qg + i * N, own);
 #pragma unroll
-            for (int i = 0; i < 9; i++) cp_async4(sf + i * NT + c, qf_ + i * N);
-          }
-        }
-        if (c < 4 && row_kind(geom, cke, L, wt, ym) == 0) {
-          const float* q = gin + off + xex;
+        for (int i = 0; i < 5; i++) cp_async4_if(d + (5 + i) * 32, qf + i * N, fneed || outer);
 #pragma unroll
-          for (int i = 0; i < 5; i++) cp_async4(sg + i * GW + xe, q + i * N);
-        }
+        for (int i = 5; i < 9; i++) cp_async4_if(d + (5 + i) * 32, qf + i * N, fneed);
       }
       cp_async_commit();
     };
-    int rs0 = 0;  // ring slot of row R
 #pragma unroll
-    for (int j = 0; j < P; j++) stage_row(y0 - 3 + j, j);
-    // own post-collision values kept for the next iteration's pull
-    float cf0 = 0.f, cG0 = 0.f, cS0 = 0.f, cS1 = 0.f, cS2 = 0.f, cS3 = 0.f;
-    double acc_n = 0.0, acc_phi = 0.0, acc_mom = 0.0;
-    // ring slots of pipeline rows R (s0), R-1 (s1), R-2 (s2) for gh and col;
-    // raw keeps four rows: R (r0), R-1 (r1), R-2 (r2), R-3 (r3)
-    int s0 = 0, s1 = 2, s2 = 1;
-    int r0 = 0, r1 = 3, r2 = 2, r3 = 1;
+    for (int j = 0; j < P; j++) stage(y0 - 3 + j, j);
 
+    // per pipeline row of the own column: raw phi of rows R, R-1, R-2
+    // (pr0..pr2), phi with ghosts of rows R-1, R-2, R-3 (pe0..pe2), kinds of
+    // rows R .. R-3 (k0..k3), mapped rows R .. R-2 (m0..m2; -1 outside a
+    // closed domain)
+    float pr0 = 0.f, pr1 = 0.f, pr2 = 0.f, pe0 = 0.f, pe1 = 0.f, pe2 = 0.f;
+    float px0 = 0.f, px1 = 0.f, px2 = 0.f;  // raw phi outside the strip (edge lanes)
+    int k0 = 1, k1 = 1, k2 = 1, k3 = 1;
+    int m0 = -1, m1 = -1, m2 = -1;
+    // post-collision f_1..8 and moving g parts P_1..4 of row R-3 (cB); of
+    // row R-4 only what the pull takes from it: f*_2, f*_5, f*_6, P_2 (cA);
+    // rest f_0*, g_0* and stay parts (1-q) g_1..4 of row R-3 (oB)
+    float cA[4], cB[12], oB[6];
+#pragma unroll
+    for (int i = 0; i < 4; i++) cA[i] = 0.f;
+#pragma unroll
+    for (int i = 0; i < 12; i++) cB[i] = 0.f;
+#pragma unroll
+    for (int i = 0; i < 6; i++) oB[i] = 0.f;
+    double acc_n = 0.0, acc_phi = 0.0, acc_mom = 0.0;
+    int sl = 0;  // ring slot of row R
+
+#pragma unroll 1
     for (int k = 0; k < ch + 6; k++) {
       const int R = y0 - 3 + k;
-      // ---------------- stage 1: phi of row R (staged P iterations ago)
       {
-        int slot = rs0 + P;
-        if (slot >= D) slot -= D;  // slot of row R+P, last used by row R-3
-        stage_row(R + P, slot);
+        int sp = sl + P;
+        if (sp >= D) sp -= D;  // the slot of row R+P is the slot of row R-3
+        stage(R + P, sp);
       }
-      cp_async_wait<P>();  // this thread's copies of row R have landed
+      cp_async_wait<P>();  // this lane's copies of row R have landed
       k3 = k2;
       k2 = k1;
       k1 = k0;
       m2 = m1;
       m1 = m0;
-      h3 = h2;
-      h2 = h1;
-      h1 = h0;
+      pr2 = pr1;
+      pr1 = pr0;
+      px2 = px1;
+      px1 = px0;
+      pe2 = pe1;
+      pe1 = pe0;
       {
         int ym;
-        const bool in = map_row(I, R, ym);
-        m0 = ym;
-        h0 = !in || (geom == GEOM_NOZZLE && strip_wall && ym < L) || (geom == GEOM_PLATE && ym < wt);
-        k0 = in ? row_kind(geom, ck, L, wt, ym) : 1;
-        const float* sg = ring + rs0 * RS;
-        if (active)
-          raw[r0 * (NT + 4) + c + 2] =
-              k0 == 0 ? sg[c + 2] + sg[GW + c + 2] + sg[2 * GW + c + 2] + sg[3 * GW + c + 2] +
-                            sg[4 * GW + c + 2]
-                      : 0.0f;
-        if (c < 4) {
-          keR = in ? row_kind(geom, cke, L, wt, ym) : 1;
-          raw[r0 * (NT + 4) + xe] =
-              keR == 0 ? sg[xe] + sg[GW + xe] + sg[2 * GW + xe] + sg[3 * GW + xe] + sg[4 * GW + xe]
-                       : 0.0f;
+        m0 = map_row_v(R, ny, bc, ym) ? ym : -1;
+        k0 = m0 >= 0 ? row_kind(geom, ck, L, wt, m0) : 1;
+        const float* sg = ring + sl * kRowFloats;
+        pr0 = k0 == 0 ? sg[0] + sg[32] + sg[64] + sg[96] + sg[128] : 0.0f;
+        px0 = edge && k0 != 0 && m0 >= 0 && row_kind(geom, cko, L, wt, m0) == 0
+                  ? sg[160] + sg[192] + sg[224] + sg[256] + sg[288]
+                  : 0.0f;
+      }
+      // ---- phi with wetting ghosts of row R-1
+      pe0 = pr1;
+      if (__any_sync(kFull, k1 != 0)) {
+        float aW = __shfl_up_sync(kFull, pr0, 1), aE = __shfl_down_sync(kFull, pr0, 1);
+        float bW = __shfl_up_sync(kFull, pr1, 1), bE = __shfl_down_sync(kFull, pr1, 1);
+        float cW = __shfl_up_sync(kFull, pr2, 1), cE = __shfl_down_sync(kFull, pr2, 1);
+        if (edge && lane == 0) {
+          aW = px0;
+          bW = px1;
+          cW = px2;
+        } else if (edge) {
+          aE = px0;
+          bE = px1;
+          cE = px2;
+        }
+        if (k1 != 0) {
+          // kinds of the neighbours in rows R (a), R-1 (b), R-2 (c)
+          const int kaW = m0 >= 0 ? row_kind(geom, ckW, L, wt, m0) : 1;
+          const int kaE = m0 >= 0 ? row_kind(geom, ckE, L, wt, m0) : 1;
+          const int kbW = m1 >= 0 ? row_kind(geom, ckW, L, wt, m1) : 1;
+          const int kbE = m1 >= 0 ? row_kind(geom, ckE, L, wt, m1) : 1;
+          const int kcW = m2 >= 0 ? row_kind(geom, ckW, L, wt, m2) : 1;
+          const int kcE = m2 >= 0 ? row_kind(geom, ckE, L, wt, m2) : 1;
+          // mean over fluid face neighbours of phi + h_s / kappa, else the
+          // plain mean over fluid diagonal neighbours
+          const float h = k1 == 2 ? hk : 0.0f;
+          float sum = 0.0f;
+          int cnt = 0;
+          if (kbE == 0) { sum += bE + h; cnt++; }
+          if (k0 == 0) { sum += pr0 + h; cnt++; }
+          if (kbW == 0) { sum += bW + h; cnt++; }
+          if (k2 == 0) { sum += pr2 + h; cnt++; }
+          if (cnt == 0) {
+            if (kaE == 0) { sum += aE; cnt++; }
+            if (kaW == 0) { sum += aW; cnt++; }
+            if (kcW == 0) { sum += cW; cnt++; }
+            if (kcE == 0) { sum += cE; cnt++; }
+          }
+          pe0 = cnt ? sum / (float)cnt : 0.0f;
         }
       }
-      int rs2 = rs0 - 2;  // ring slot of row R-2
-      if (rs2 < 0) rs2 += D;
-      __syncthreads();
-      // ---------------- stage 2: ghost values of row R-1 (rows with solids)
-      if (k >= 2 && h1) {
-        const float* ra = raw + r2 * (NT + 4);  // row R-2
-        const float* rb = raw + r1 * (NT + 4);  // row R-1
-        const float* rc = raw + r0 * (NT + 4);  // row R
-        float* go = gh + s1 * (NT + 2);
-        if (active) {
-          const int j = c + 1;
-          float v;
-          if (k1 == 0) {
-            v = rb[j + 1];
-          } else {
-            float w[9] = {ra[j], ra[j + 1], ra[j + 2], rb[j], rb[j + 1], rb[j + 2],
-                          rc[j], rc[j + 1], rc[j + 2]};
-            v = ghost_rule(I, k1, x, R - 1, w);
-          }
-          go[j] = v;
-        }
-        if (c < 2) {
-          const int j = xg;
-          int ym;
-          const int kk = map_row(I, R - 1, ym) ? row_kind(geom, ckg, L, wt, ym) : 1;
-          float v;
-          if (kk == 0) {
-            v = rb[j + 1];
-          } else {
-            float w[9] = {ra[j], ra[j + 1], ra[j + 2], rb[j], rb[j + 1], rb[j + 2],
-                          rc[j], rc[j + 1], rc[j + 2]};
-            v = ghost_rule(I, kk, xgx, R - 1, w);
-          }
-          go[j] = v;
-        }
-        __syncthreads();
-      }
-      // ---------------- stage 3: collision of row R-2
-      const float pf0 = cf0, pG0 = cG0, pS0 = cS0, pS1 = cS1, pS2 = cS2, pS3 = cS3;
-      double dw = 0.0, dm = 0.0, dp = 0.0;
+      // ---- collision of row Rc = R-2 into cn / on
       const int Rc = R - 2;
-      if (k >= 4 && active && k2 == 0) {
-        const float* sg2 = ring + rs2 * RS;  // g and f of row Rc, own column
-        float g2[5], fr[9];
+      float cn[12], on[6];
+      {
+        const float nW = __shfl_up_sync(kFull, pe0, 1), nE = __shfl_down_sync(kFull, pe0, 1);
+        const float cW = __shfl_up_sync(kFull, pe1, 1), cE = __shfl_down_sync(kFull, pe1, 1);
+        const float sW = __shfl_up_sync(kFull, pe2, 1), sE = __shfl_down_sync(kFull, pe2, 1);
+        double dw = 0.0, dm = 0.0, dp = 0.0;
+        if (k >= 4 && col_lane && k2 == 0) {
+          int s2 = sl - 2;
+          if (s2 < 0) s2 += D;
+          const float* sg = ring + s2 * kRowFloats;
+          float g2[5], fr[9];
 #pragma unroll
-        for (int i = 0; i < 5; i++) g2[i] = sg2[i * GW + c + 2];
+          for (int i = 0; i < 5; i++) g2[i] = sg[i * 32];
 #pragma unroll
-        for (int i = 0; i < 9; i++) fr[i] = sg2[5 * GW + i * NT + c];
-        // phi with ghosts of rows Rc-1 (slot of R-3 = slot of R), Rc, Rc+1;
-        // a row without solid cells is read from raw (one column shifted)
-        const float* hb = h3 ? gh + s0 * (NT + 2) : raw + r3 * (NT + 4) + 1;
-        const float* hc = h2 ? gh + s2 * (NT + 2) : raw + r2 * (NT + 4) + 1;
-        const float* ht = h1 ? gh + s1 * (NT + 2) : raw + r1 * (NT + 4) + 1;
-        const int j = c + 1;
-        const float pC = hc[j];
-        const float pE = hc[j + 1], pW = hc[j - 1], pN = ht[j], pS = hb[j];
-        const float pNE = ht[j + 1], pNW = ht[j - 1], pSW = hb[j - 1], pSE = hb[j + 1];
-        // lap = 6 sum_i w_i (phi_i - phi) from the differences, which are
-        // exact where neighbours are close (no cancellation of O(10) terms)
-        const float lap = (2.0f / 3.0f) * ((pE - pC) + (pN - pC) + (pW - pC) + (pS - pC)) +
-                          (1.0f / 6.0f) * ((pNE - pC) + (pNW - pC) + (pSW - pC) + (pSE - pC));
-        const float gx = (pE - pW) * (1.0f / 3.0f) + (pNE - pNW - pSW + pSE) * (1.0f / 12.0f);
-        const float gy = (pN - pS) * (1.0f / 3.0f) + (pNE + pNW - pSW - pSE) * (1.0f / 12.0f);
-        const float phi = g2[0] + g2[1] + g2[2] + g2[3] + g2[4];
-        const float mu = A4 * phi * ((phi - I.phis) * (phi + I.phis)) - kappa * lap;
-        float C = 0.5f * (phi * inv_phis + 1.0f);
-        C = fminf(fmaxf(C, 0.0f), 1.0f);
-        const float Fb = (drive_col && m2 < L) || geom != GEOM_NOZZLE ? Fd * C : 0.0f;
-        const float Fx = mu * gx, Fy = mu * gy + Fb;
-        // fr holds deviations f_i - w_i n0: their sum is n - n0
-        const float dn = fr[0] + fr[1] + fr[2] + fr[3] + fr[4] + fr[5] + fr[6] + fr[7] + fr[8];
-        const float n = n0 + dn;
-        const float mx = fr[1] - fr[3] + fr[5] - fr[6] - fr[7] + fr[8];
-        const float my = fr[2] - fr[4] + fr[5] + fr[6] - fr[7] - fr[8];
-        const float inv_n = 1.0f / n;
-        const float ux = (mx + 0.5f * Fx) * inv_n, uy = (my + 0.5f * Fy) * inv_n;
-        const float u2 = ux * ux + uy * uy;
-        if (!(u2 < 0.09f)) atomicOr(I.status, kStatusNumeric);
-        const float om = 1.0f / (0.5f + 3.0f * (nu_air + C * dnu));
-        const float pref = 3.0f * (1.0f - 0.5f * om);
-        // A_i - n0 = 3 (phi mu + n / 3) - n0 for i >= 1 (Eq. 6), on deviations
-        const float p3 = dn + 3.0f * phi * mu;
-        const float uF = ux * Fx + uy * Fy;
-        const float base = -1.5f * u2;  // velocity-independent part of the bracket of Eq. 5
-        // Moving directions first (deviations feq_i - w_i n0); the rest
-        // direction then takes the balance, feq_0 - w_0 n0 = (n - n0) -
-        // sum_{i>=1} (feq_i - w_i n0) and F_0 = -sum_{i>=1} F_i.  This equals
-        // A_0 = 9n/4 - 15 p / 4 of Eq. 6 (the moments of Eq. 5-6 and of the
-        // forcing term are exact) but conserves mass in FP32, whose rounded
-        // weights 4/9, 1/9, 1/36 do not sum to one.
-        // Opposite directions i, i' share the even part of the equilibrium
-        // and of the forcing term and differ in the sign of the odd part:
-        // feq = E +- O, F = FE +- FO with E = w (p3 + n (base + 4.5 cu^2)),
-        // O = 3 w n cu, FE = w pref (3 cu cF - uF), FO = w pref cF.
-        float fs[9];
-        float sum_eq = 0.0f, sum_F = 0.0f;
-        const float n3 = 3.0f * n;
+          for (int i = 0; i < 9; i++) fr[i] = sg[(5 + i) * 32];
+          const float pC = pe1;
+          // lap = 6 sum_i w_i (phi_i - phi) from the differences, which are
+          // exact where neighbours are close (no cancellation of O(10) terms)
+          const float lap = (2.0f / 3.0f) * ((cE - pC) + (pe0 - pC) + (cW - pC) + (pe2 - pC)) +
+                            (1.0f / 6.0f) * ((nE - pC) + (nW - pC) + (sW - pC) + (sE - pC));
+          const float gx = (cE - cW) * (1.0f / 3.0f) + (nE - nW - sW + sE) * (1.0f / 12.0f);
+          const float gy = (pe0 - pe2) * (1.0f / 3.0f) + (nE + nW - sW - sE) * (1.0f / 12.0f);
+          const float phi = pr2;  // sum of g2 in the same order (raw phi of row R-2)
+          const float mu = A4 * phi * ((phi - phis) * (phi + phis)) - kappa * lap;
+          float C = 0.5f * (phi * inv_phis + 1.0f);
+          C = fminf(fmaxf(C, 0.0f), 1.0f);
+          const float Fb = (drive_col && m2 < L) || geom != GEOM_NOZZLE ? Fd * C : 0.0f;
+          const float Fx = mu * gx, Fy = mu * gy + Fb;
+          // fr holds deviations f_i - w_i n0: their sum is n - n0
+          const float dn = fr[0] + fr[1] + fr[2] + fr[3] + fr[4] + fr[5] + fr[6] + fr[7] + fr[8];
+          const float n = n0 + dn;
+          const float mx = fr[1] - fr[3] + fr[5] - fr[6] - fr[7] + fr[8];
+          const float my = fr[2] - fr[4] + fr[5] + fr[6] - fr[7] - fr[8];
+          const float inv_n = 1.0f / n;
+          const float ux = (mx + 0.5f * Fx) * inv_n, uy = (my + 0.5f * Fy) * inv_n;
+          const float u2 = ux * ux + uy * uy;
+          if (!(u2 < 0.09f)) atomicOr(I.status, kStatusNumeric);
+          const float om = 1.0f / (0.5f + 3.0f * (nu_air + C * dnu));
+          const float pref = 3.0f * (1.0f - 0.5f * om);
+          // A_i - n0 = 3 (phi mu + n / 3) - n0 for i >= 1 (Eq. 6), on deviations
+          const float p3 = dn + 3.0f * phi * mu;
+          const float uF = ux * Fx + uy * Fy;
+          const float base = -1.5f * u2;  // velocity-independent part of the bracket of Eq. 5
+          // Moving directions first (deviations feq_i - w_i n0); the rest
+          // direction then takes the balance, feq_0 - w_0 n0 = (n - n0) -
+          // sum_{i>=1} (feq_i - w_i n0) and F_0 = -sum_{i>=1} F_i.  This equals
+          // A_0 of Eq. 6 (the moments of Eq. 5-6 and of the forcing term are
+          // exact) but conserves mass in FP32, whose rounded weights 4/9,
+          // 1/9, 1/36 do not sum to one.  Opposite directions i, i' share the
+          // even part of the equilibrium and of the forcing term and differ
+          // in the sign of the odd part: feq = E +- O, F = FE +- FO with
+          // E = w (p3 + n (base + 4.5 cu^2)), O = 3 w n cu,
+          // FE = w pref (3 cu cF - uF), FO = w pref cF.
+          float fs[9];
+          float sum_eq = 0.0f, sum_F = 0.0f;
+          const float n3 = 3.0f * n;
 #pragma unroll
-        for (int i = 1; i < 9; i++) {
-          if (i == 3 || i == 4 || i == 7 || i == 8) continue;  // handled with its pair
-          const int ib = i == 1 ? 3 : (i == 2 ? 4 : (i == 5 ? 7 : 8));
-          const float w = i < 5 ? W1 : W2;
-          const float ex = (float)cEX(i), ey = (float)cEY(i);
-          const float cu = ex * ux + ey * uy;
-          const float cF = ex * Fx + ey * Fy;
-          const float E = w * (p3 + n * (base + 4.5f * cu * cu));
-          const float O = (w * n3) * cu;
-          const float wp = w * pref;
-          const float FE = wp * (3.0f * cu * cF - uF);
-          const float FO = wp * cF;
-          sum_eq += 2.0f * E;
-          sum_F += 2.0f * FE;
-          fs[i] = fr[i] + om * ((E + O) - fr[i]) + (FE + FO);
-          fs[ib] = fr[ib] + om * ((E - O) - fr[ib]) + (FE - FO);
-        }
-        fs[0] = fr[0] + om * ((dn - sum_eq) - fr[0]) - sum_F;
-        // order parameter: Eq. 9-10 with the rest direction special
-        const float gmu = gamma * mu;
-        const float pq = phi * inv2q;
-        float* cl = col + s2 * 12 * NT;
+          for (int i = 1; i < 9; i++) {
+            if (i == 3 || i == 4 || i == 7 || i == 8) continue;  // handled with its pair
+            const int ib = i == 1 ? 3 : (i == 2 ? 4 : (i == 5 ? 7 : 8));
+            const float w = i < 5 ? W1 : W2;
+            const float ex = (float)cEX(i), ey = (float)cEY(i);
+            const float cu = ex * ux + ey * uy;
+            const float cF = ex * Fx + ey * Fy;
+            const float E = w * (p3 + n * (base + 4.5f * cu * cu));
+            const float O = (w * n3) * cu;
+            const float wp = w * pref;
+            const float FE = wp * (3.0f * cu * cF - uF);
+            const float FO = wp * cF;
+            sum_eq += 2.0f * E;
+            sum_F += 2.0f * FE;
+            fs[i] = fr[i] + om * ((E + O) - fr[i]) + (FE + FO);
+            fs[ib] = fr[ib] + om * ((E - O) - fr[ib]) + (FE - FO);
+          }
+          fs[0] = fr[0] + om * ((dn - sum_eq) - fr[0]) - sum_F;
 #pragma unroll
-        for (int i = 1; i < 9; i++) cl[(i - 1) * NT + c] = fs[i];
-        float sum_ge = 0.0f;
-        float S[4];
+          for (int i = 1; i < 9; i++) cn[i - 1] = fs[i];
+          // order parameter: Eq. 9-10 with the rest direction special; the
+          // moving part q g_i + Omega_i streams, (1 - q) g_i stays
+          const float gmu = gamma * mu;
+          const float pq = phi * inv2q;
+          float sum_ge = 0.0f;
 #pragma unroll
-        for (int i = 1; i < 5; i++) {
-          const float cu = (float)cEX(i) * ux + (float)cEY(i) * uy;
-          const float ge = 0.5f * gmu + pq * cu;
-          sum_ge += ge;
-          const float omi = (ge - g2[i]) * inv_tphi;
-          cl[(7 + i) * NT + c] = qf * g2[i] + omi;
-          S[i - 1] = omq * g2[i];
+          for (int i = 1; i < 5; i++) {
+            const float cu = (float)cEX(i) * ux + (float)cEY(i) * uy;
+            const float ge = 0.5f * gmu + pq * cu;
+            sum_ge += ge;
+            cn[7 + i] = qf * g2[i] + (ge - g2[i]) * inv_tphi;
+            on[1 + i] = omq * g2[i];
+          }
+          // rest direction: g0_0 = phi - sum_{i>=1} g0_i (Eq. 10 as a
+          // balance, so that sum g0 = phi exactly); with phi - g_0 =
+          // sum_{i>=1} g_i the relaxation uses small terms only
+          on[0] = fs[0];
+          on[1] = g2[0] + ((g2[1] + g2[2] + g2[3] + g2[4]) - sum_ge) * inv_tphi;
+          if (DIAG && out_lane && Rc >= y0 && Rc < y0 + ch) {
+            const float e = fminf(fmaxf(phi * inv_phis, 0.0f), 1.0f);
+            dw = (double)e;
+            dm = (double)e * (double)n;
+            dp = dm * (double)uy;
+            acc_n += (double)n;
+            acc_phi += (double)phi;
+            acc_mom += (double)n * (double)uy;
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < 12; i++) cn[i] = 0.f;
+#pragma unroll
+          for (int i = 0; i < 6; i++) on[i] = 0.f;
         }
-        cS0 = S[0];
-        cS1 = S[1];
-        cS2 = S[2];
-        cS3 = S[3];
-        // rest direction: g0_0 = phi - 2 Gamma mu (Eq. 10), taken as the
-        // balance phi - sum_{i>=1} g0_i so that sum g0 = phi exactly; with
-        // phi - g_0 = sum_{i>=1} g_i the relaxation uses small terms only
-        // (no difference of two rounded values of size phi*)
-        const float om0 = ((g2[1] + g2[2] + g2[3] + g2[4]) - sum_ge) * inv_tphi;
-        cf0 = fs[0];
-        cG0 = g2[0] + om0;
-        if (DIAG && owned && Rc >= y0 && Rc < y0 + ch) {
-          const float e = fminf(fmaxf(phi * inv_phis, 0.0f), 1.0f);
-          dw = (double)e;
-          dm = (double)e * (double)n;
-          dp = dm * (double)uy;
-          acc_n += (double)n;
-          acc_phi += (double)phi;
-          acc_mom += (double)n * (double)uy;
-        }
-      }
-      if (DIAG && k >= 4 && Rc >= y0 && Rc < y0 + ch) {
-        dw = warp_sum(dw);
-        dm = warp_sum(dm);
-        dp = warp_sum(dp);
-        if ((c & 31) == 0) {
-          red[(c >> 5) * 3 + 0] = dw;
-          red[(c >> 5) * 3 + 1] = dm;
-          red[(c >> 5) * 3 + 2] = dp;
-        }
-      }
-      __syncthreads();
-      if (DIAG && c == 0 && k >= 4 && Rc >= y0 && Rc < y0 + ch) {
-        double sw = 0, sm = 0, sp = 0;
-        for (int wq = 0; wq < NT / 32; wq++) {
-          sw += red[wq * 3 + 0];
-          sm += red[wq * 3 + 1];
-          sp += red[wq * 3 + 2];
-        }
-        atomicAdd(I.rows + Rc, sw);
-        atomicAdd(I.rows + ny + Rc, sm);
-        atomicAdd(I.rows + 2 * ny + Rc, sp);
-      }
-      // ---------------- stage 4: streaming of row R-3
-      if (k >= 6 && owned && k3 == 0) {
-        const int Y = R - 3;
-        const float* cb = col + s1 * 12 * NT;  // row Y-1 (slot of R-4 = slot of R-1)
-        const float* cm = col + s0 * 12 * NT;  // row Y   (slot of R-3 = slot of R)
-        const float* ct = col + s2 * 12 * NT;  // row Y+1 (slot of R-2)
-        const int cw = it.single ? (c == 0 ? wc - 1 : c - 1) : c - 1;
-        const int ce = it.single ? (c == wc - 1 ? 0 : c + 1) : c + 1;
-        float fn[9];
-        fn[0] = pf0;
-        // pull f_i(Y) = f*_i(Y - c_i); g_i(Y) = (1-q) g_i(Y) + P_i(Y - c_i)
-        fn[1] = cm[0 * NT + cw];
-        fn[2] = cb[1 * NT + c];
-        fn[3] = cm[2 * NT + ce];
-        fn[4] = ct[3 * NT + c];
-        fn[5] = cb[4 * NT + cw];
-        fn[6] = cb[5 * NT + ce];
-        fn[7] = ct[6 * NT + ce];
-        fn[8] = ct[7 * NT + cw];
-        float P1 = cm[8 * NT + cw], P2 = cb[9 * NT + c], P3 = cm[10 * NT + ce], P4 = ct[11 * NT + c];
-        if (near_solid(I, colwall, Y)) {
-          // halfway bounce-back: a population whose source is solid is the
-          // cell's own post-collision population of the opposite direction
-          const unsigned sm = solid_sources(I, x, Y);
-          if (sm) {
-            if (sm & (1u << 1)) { fn[1] = cm[2 * NT + c]; P1 = cm[10 * NT + c]; }
-            if (sm & (1u << 2)) { fn[2] = cm[3 * NT + c]; P2 = cm[11 * NT + c]; }
-            if (sm & (1u << 3)) { fn[3] = cm[0 * NT + c]; P3 = cm[8 * NT + c]; }
-            if (sm & (1u << 4)) { fn[4] = cm[1 * NT + c]; P4 = cm[9 * NT + c]; }
-            if (sm & (1u << 5)) fn[5] = cm[6 * NT + c];
-            if (sm & (1u << 6)) fn[6] = cm[7 * NT + c];
-            if (sm & (1u << 7)) fn[7] = cm[4 * NT + c];
-            if (sm & (1u << 8)) fn[8] = cm[5 * NT + c];
+        if (DIAG && k >= 4 && Rc >= y0 && Rc < y0 + ch) {
+          dw = warp_sum(dw);
+          dm = warp_sum(dm);
+          dp = warp_sum(dp);
+          if (lane == 0) {
+            atomicAdd(I.rows + Rc, dw);
+            atomicAdd(I.rows + ny + Rc, dm);
+            atomicAdd(I.rows + 2 * ny + Rc, dp);
           }
         }
-        float* fo = fout + Y * nx + x;
-        float* go = gout + Y * nx + x;
-#pragma unroll
-        for (int i = 0; i < 9; i++) fo[i * N] = fn[i];
-        go[0] = pG0;
-        go[N] = pS0 + P1;
-        go[2 * N] = pS1 + P2;
-        go[3 * N] = pS2 + P3;
-        go[4 * N] = pS3 + P4;
       }
-      // rotate the ring slots: the slot of R-2 becomes the slot of R+1
-      const int sn = s2;
-      s2 = s1;
-      s1 = s0;
-      s0 = sn;
-      rs0 = rs0 + 1 == D ? 0 : rs0 + 1;
-      const int rn = r3;
-      r3 = r2;
-      r2 = r1;
-      r1 = r0;
-      r0 = rn;
+      // ---- streaming of row Y = R-3: pull f_i(Y) = f*_i(Y - c_i) and
+      // g_i(Y) = (1 - q) g_i(Y) + P_i(Y - c_i); rows Y-1 (cA), Y (cB), Y+1 (cn)
+      {
+        const float w1 = __shfl_up_sync(kFull, cB[0], 1), w5 = __shfl_up_sync(kFull, cA[1], 1);
+        const float w8 = __shfl_up_sync(kFull, cn[7], 1), wP1 = __shfl_up_sync(kFull, cB[8], 1);
+        const float e3 = __shfl_down_sync(kFull, cB[2], 1), e6 = __shfl_down_sync(kFull, cA[2], 1);
+        const float e7 = __shfl_down_sync(kFull, cn[6], 1), eP3 = __shfl_down_sync(kFull, cB[10], 1);
+        if (k >= 6 && out_lane && k3 == 0) {
+          const int Y = R - 3;
+          float fn[9];
+          fn[0] = oB[0];
+          fn[1] = w1;
+          fn[2] = cA[0];
+          fn[3] = e3;
+          fn[4] = cn[3];
+          fn[5] = w5;
+          fn[6] = e6;
+          fn[7] = e7;
+          fn[8] = w8;
+          float P1 = wP1, P2 = cA[3], P3 = eP3, P4 = cn[11];
+          if (near_solid_v(geom, bc, ny, L, wt, colwall, Y)) {
+            // halfway bounce-back: a population whose source is solid is the
+            // cell's own post-collision population of the opposite direction
+            const unsigned sm = solid_sources(I, x, Y);
+            if (sm) {
+              if (sm & (1u << 1)) { fn[1] = cB[2]; P1 = cB[10]; }
+              if (sm & (1u << 2)) { fn[2] = cB[3]; P2 = cB[11]; }
+              if (sm & (1u << 3)) { fn[3] = cB[0]; P3 = cB[8]; }
+              if (sm & (1u << 4)) { fn[4] = cB[1]; P4 = cB[9]; }
+              if (sm & (1u << 5)) fn[5] = cB[6];
+              if (sm & (1u << 6)) fn[6] = cB[7];
+              if (sm & (1u << 7)) fn[7] = cB[4];
+              if (sm & (1u << 8)) fn[8] = cB[5];
+            }
+          }
+          float* fo = fout + Y * nx + x;
+          float* go = gout + Y * nx + x;
+#pragma unroll
+          for (int i = 0; i < 9; i++) fo[i * N] = fn[i];
+          go[0] = oB[1];
+          go[N] = oB[2] + P1;
+          go[2 * N] = oB[3] + P2;
+          go[3 * N] = oB[4] + P3;
+          go[4 * N] = oB[5] + P4;
+        }
+      }
+      cA[0] = cB[1];  // f*_2
+      cA[1] = cB[4];  // f*_5
+      cA[2] = cB[5];  // f*_6
+      cA[3] = cB[9];  // P_2
+#pragma unroll
+      for (int i = 0; i < 12; i++) cB[i] = cn[i];
+#pragma unroll
+      for (int i = 0; i < 6; i++) oB[i] = on[i];
+      sl = sl + 1 == D ? 0 : sl + 1;
     }
-    cp_async_wait<0>();  // no copy may land after the block moves on
+    cp_async_wait<0>();  // no copy may land after the warp moves on
     if (DIAG) {
-      // lattice sums of this item, one atomic per warp (every lane of the
-      // block takes part; the block size is a multiple of 32)
-      double a = warp_sum(acc_n), b = warp_sum(acc_phi), m = warp_sum(acc_mom);
-      if ((c & 31) == 0) {
+      const double a = warp_sum(acc_n), b = warp_sum(acc_phi), m = warp_sum(acc_mom);
+      if (lane == 0) {
         atomicAdd(I.sums + 0, a);
         atomicAdd(I.sums + 1, b);
         atomicAdd(I.sums + 2, m);
       }
     }
-    __syncthreads();
   }
 }
-
-#undef phis2
-#undef inv_phis
-#undef A4
-#undef kappa
-#undef qf
-#undef omq
-#undef inv_tphi
-#undef gamma
-#undef inv2q
-#undef nu_air
-#undef dnu
-#undef n0
 
 // ---------------------------------------------------------------------------
 // Initialisation (FP64): phi_0 of the chosen profile into a temporary.
@@ -865,11 +830,8 @@ __global__ void f_convert_kernel(const Inst* __restrict__ insts, int index, cons
 }  // namespace
 
 // ---------------------------------------------------------------------------
-size_t step_smem_bytes(int nt, int prefetch) {
-  // nt is a multiple of 32, so the float part keeps the doubles 8-byte aligned
-  size_t ring = (size_t)(prefetch + 3) * (5 * (size_t)(nt + 4) + 9 * (size_t)nt);
-  size_t floats = ring + 4 * (size_t)(nt + 4) + 3 * (size_t)(nt + 2) + 36 * (size_t)nt;
-  return floats * sizeof(float) + (size_t)(nt / 32) * 3 * sizeof(double);
+size_t step_smem_bytes(int nthreads, int prefetch) {
+  return (size_t)(nthreads / 32) * (prefetch + 3) * kRowFloats * sizeof(float);
 }
 
 cudaError_t launch_init(const Inst* d_inst, const Inst& h, int index, cudaStream_t s) {
@@ -880,24 +842,6 @@ cudaError_t launch_init(const Inst* d_inst, const Inst& h, int index, cudaStream
   const size_t N = (size_t)h.nx * h.ny;
   zero_kernel<<<256, 256, 0, s>>>(h.f[1], 9 * N);
   zero_kernel<<<256, 256, 0, s>>>(h.g[1], 5 * N);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_step(const Inst* d_inst, const Item* d_items, int n_items, int nthreads,
-                        int grid, const long long* d_t, int t_off, bool diag, int prefetch,
-                        cudaStream_t s) {
-  const size_t smem = step_smem_bytes(nthreads, prefetch);
-  if (prefetch == 1) {
-    if (diag)
-      step_kernel<true, 1><<<grid, nthreads, smem, s>>>(d_inst, d_items, n_items, d_t, t_off);
-    else
-      step_kernel<false, 1><<<grid, nthreads, smem, s>>>(d_inst, d_items, n_items, d_t, t_off);
-  } else {
-    if (diag)
-      step_kernel<true, 2><<<grid, nthreads, smem, s>>>(d_inst, d_items, n_items, d_t, t_off);
-    else
-      step_kernel<false, 2><<<grid, nthreads, smem, s>>>(d_inst, d_items, n_items, d_t, t_off);
-  }
   return cudaGetLastError();
 }
 
@@ -932,20 +876,74 @@ cudaError_t launch_f_import(const Inst* d_inst, const Inst& h, int index, const 
   return cudaGetLastError();
 }
 
-int step_prefetch_for(int nthreads) {
-  return 2 * step_smem_bytes(nthreads, 2) <= 227 * 1024 ? 2 : 1;
+template <bool DIAG>
+cudaError_t launch_step_p(const Inst* d_inst, const Item* d_items, int n_items, int nthreads,
+                          int grid, const long long* d_t, int t_off, int prefetch, size_t smem,
+                          cudaStream_t s) {
+  switch (prefetch) {
+    case 1:
+      step_kernel<DIAG, 1><<<grid, nthreads, smem, s>>>(d_inst, d_items, n_items, d_t, t_off);
+      break;
+    case 2:
+      step_kernel<DIAG, 2><<<grid, nthreads, smem, s>>>(d_inst, d_items, n_items, d_t, t_off);
+      break;
+    case 3:
+      step_kernel<DIAG, 3><<<grid, nthreads, smem, s>>>(d_inst, d_items, n_items, d_t, t_off);
+      break;
+    default:
+      step_kernel<DIAG, 4><<<grid, nthreads, smem, s>>>(d_inst, d_items, n_items, d_t, t_off);
+      break;
+  }
+  return cudaGetLastError();
 }
 
+cudaError_t launch_step(const Inst* d_inst, const Item* d_items, int n_items, int nthreads,
+                        int grid, const long long* d_t, int t_off, bool diag, int prefetch,
+                        cudaStream_t s) {
+  if (nthreads != kStepThreads || prefetch < 1 || prefetch > kMaxPrefetch)
+    return cudaErrorInvalidValue;
+  if (n_items <= 0) return cudaSuccess;
+  const size_t smem = step_smem_bytes(nthreads, prefetch);
+  return diag ? launch_step_p<true>(d_inst, d_items, n_items, nthreads, grid, d_t, t_off, prefetch,
+                                    smem, s)
+              : launch_step_p<false>(d_inst, d_items, n_items, nthreads, grid, d_t, t_off,
+                                     prefetch, smem, s);
+}
+
+int step_prefetch_for(int) { return 3; }
+
 cudaError_t set_step_smem_limit() {
-  const int lim = (int)step_smem_bytes(256, 2);
-  cudaError_t e = cudaFuncSetAttribute(step_kernel<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(step_kernel<false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(step_kernel<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(step_kernel<false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  const int lim = (int)step_smem_bytes(kStepThreads, kMaxPrefetch);
+  cudaError_t e = cudaSuccess;
+#define SET_LIM(DG, PF)                                                                      \
+  if (e == cudaSuccess)                                                                      \
+    e = cudaFuncSetAttribute(step_kernel<DG, PF>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  SET_LIM(true, 1) SET_LIM(false, 1) SET_LIM(true, 2) SET_LIM(false, 2)
+  SET_LIM(true, 3) SET_LIM(false, 3) SET_LIM(true, 4) SET_LIM(false, 4)
+#undef SET_LIM
   return e;
+}
+
+int make_items(const Inst& I, int k, int chunk, Item* out, int cap) {
+  constexpr int halo = 2, W = 32 - 2 * halo;  // 28 written columns per strip
+  const int nstrip = (I.nx + W - 1) / W;
+  int n = 0;
+  for (int y0 = 0; y0 < I.ny; y0 += chunk)
+    for (int s = 0; s < nstrip; s++) {
+      if (n >= cap) return -1;
+      Item& it = out[n++];
+      it.inst = k;
+      it.xs = s * W;
+      it.nout = I.nx - s * W < W ? I.nx - s * W : W;
+      it.halo = halo;
+      it.y0 = y0;
+      it.ch = I.ny - y0 < chunk ? I.ny - y0 : chunk;
+    }
+  return n;
+}
+
+int items_per_lattice(const Inst& I, int chunk) {
+  return ((I.nx + 27) / 28) * ((I.ny + chunk - 1) / chunk);
 }
 
 }  // namespace ij

@@ -19,6 +19,7 @@ the library's kernels; this module only marshals arguments and orchestrates
 the two paths.
 """
 import ctypes as C
+import hashlib
 
 import numpy as np
 
@@ -216,8 +217,16 @@ def sample_inputs(n, seed):
     return x
 
 
-def lattice_params(row, seed=0):
+def row_seed(row):
+    """Jitter seed of an input row: a hash of its values, so that a query
+    gets the same lattice (and the same outcome) wherever it is run."""
+    digest = hashlib.blake2b(np.asarray(row, dtype=np.float64).tobytes(), digest_size=8).digest()
+    return int.from_bytes(digest, "little")
+
+
+def lattice_params(row, seed=None):
     theta, sigma, F0, T1, T2, T_idle, w = [float(v) for v in row]
+    seed = row_seed(row) if seed is None else seed
     w = int(round(w))
     return dict(nx=4 * w, ny=24 * w, geometry=W.GEOM_NOZZLE, nozzle_width=w, nozzle_length=3 * w,
                 wall_thickness=4, rho_ink=10.0, rho_air=1.0, nu_ink=0.1, nu_air=0.05, sigma=sigma,
@@ -244,7 +253,7 @@ def lbm_outcomes(rows, steps=5000, stream=None, chunk=1024):
     out = np.empty((len(rows), N_OUT))
     for a in range(0, len(rows), chunk):
         part = rows[a:a + chunk]
-        h = ij.ij_create([lattice_params(r, seed=a + k) for k, r in enumerate(part)], stream=stream)
+        h = ij.ij_create([lattice_params(r) for r in part], stream=stream)
         ij.ij_step(h, steps)
         for k in range(len(part)):
             out[a + k] = outcomes_from_history(ij.ij_history(h, k))

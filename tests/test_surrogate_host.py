@@ -48,3 +48,10 @@ def test_outcomes_are_averaged_over_the_window_after_breakup():
 def test_no_breakup_or_too_late_gives_nan():
     assert np.isnan(S.outcomes_from_history(_history(-1))).all()
     assert np.isnan(S.outcomes_from_history(_history(1950.0))).all()
+
+
+def test_row_seed_is_a_function_of_the_row():
+    a = S.sample_inputs(4, 9)
+    assert S.row_seed(a[0]) == S.row_seed(a[0].copy())
+    assert len({S.row_seed(r) for r in a}) == 4
+    assert S.lattice_params(a[1])["seed"] == S.row_seed(a[1])
