@@ -106,26 +106,6 @@ __device__ __forceinline__ int kind_at(const Inst& I, int x, int y) {
   return geom_kind(I, wrapi(x, I.nx), ym);
 }
 
-// Conservative test: may a fluid cell (x, y) have a solid neighbour?
-__device__ __forceinline__ bool near_solid(const Inst& I, bool colwall, int y) {
-  if (I.bc == BC_CLOSED && (y == 0 || y == I.ny - 1)) return true;
-  if (I.geom == GEOM_NOZZLE) {
-    if (!colwall) return false;
-    if (I.bc == BC_PER && (y == 0 || y == I.ny - 1)) return true;
-    return y - 1 < I.L;
-  }
-  if (I.geom == GEOM_PLATE) {
-    if (I.bc == BC_PER && (y == 0 || y == I.ny - 1)) return true;
-    return y - 1 < I.wt;
-  }
-  return false;
-}
-
-__device__ __forceinline__ bool in_drive(const Inst& I, int x, int ym) {
-  if (I.geom == GEOM_NOZZLE) return x >= I.cx0 && x < I.cx1 && ym < I.L;
-  return true;
-}
-
 // Fig. 1 waveform: +F0, then -F_neg, then idle (periodic if T_idle > 0).
 __device__ __forceinline__ float drive_at(const Inst& I, long long t) {
   long long tt = t;
@@ -135,13 +115,8 @@ __device__ __forceinline__ float drive_at(const Inst& I, long long t) {
   return 0.0f;
 }
 
-// Asynchronous 4-byte global -> shared copies (cp.async), grouped per row.
-__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(src) : "memory");
-}
-// The same copy issued only when pred is set (a predicated instruction, no
-// branch).
+// Asynchronous 4-byte global -> shared copy (cp.async), issued only when
+// pred is set (a predicated instruction, no branch).
 __device__ __forceinline__ void cp_async4_if(float* dst, const float* src, bool pred) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
   asm volatile(
@@ -163,11 +138,6 @@ __device__ __noinline__ unsigned solid_sources(const Inst& I, int x, int y) {
   for (int i = 1; i < 9; i++)
     if (kind_at(I, x - cEX(i), y - cEY(i)) != 0) m |= 1u << i;
   return m;
-}
-
-__device__ __forceinline__ double warp_sum(double v) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  return v;
 }
 
 // Kind of the in-domain cell (column kind colk, row ym): 0 fluid, 1 solid,
@@ -374,7 +344,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kStepBlocksPerSM)
         const float nW = __shfl_up_sync(kFull, pe0, 1), nE = __shfl_down_sync(kFull, pe0, 1);
         const float cW = __shfl_up_sync(kFull, pe1, 1), cE = __shfl_down_sync(kFull, pe1, 1);
         const float sW = __shfl_up_sync(kFull, pe2, 1), sE = __shfl_down_sync(kFull, pe2, 1);
-        double dw = 0.0, dm = 0.0, dp = 0.0;
+        // diagnostics of this cell: ink weight e, e n, e n u_y, n, phi, n u_y
+        float dg[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if (k >= 4 && col_lane && k2 == 0) {
           int s2 = sl - 2;
           if (s2 < 0) s2 += D;
@@ -466,12 +437,12 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kStepBlocksPerSM)
           on[1] = g2[0] + ((g2[1] + g2[2] + g2[3] + g2[4]) - sum_ge) * inv_tphi;
           if (DIAG && out_lane && Rc >= y0 && Rc < y0 + ch) {
             const float e = fminf(fmaxf(phi * inv_phis, 0.0f), 1.0f);
-            dw = (double)e;
-            dm = (double)e * (double)n;
-            dp = dm * (double)uy;
-            acc_n += (double)n;
-            acc_phi += (double)phi;
-            acc_mom += (double)n * (double)uy;
+            dg[0] = e;
+            dg[1] = e * n;
+            dg[2] = dg[1] * uy;
+            dg[3] = n;
+            dg[4] = phi;
+            dg[5] = n * uy;
           }
         } else {
 #pragma unroll
@@ -480,13 +451,19 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kStepBlocksPerSM)
           for (int i = 0; i < 6; i++) on[i] = 0.f;
         }
         if (DIAG && k >= 4 && Rc >= y0 && Rc < y0 + ch) {
-          dw = warp_sum(dw);
-          dm = warp_sum(dm);
-          dp = warp_sum(dp);
+          // the strip's 28 cells of the row are summed in FP32, every
+          // total across strips, rows and chunks in FP64
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int j = 0; j < 6; j++) dg[j] += __shfl_down_sync(kFull, dg[j], o);
           if (lane == 0) {
-            atomicAdd(I.rows + Rc, dw);
-            atomicAdd(I.rows + ny + Rc, dm);
-            atomicAdd(I.rows + 2 * ny + Rc, dp);
+            atomicAdd(I.rows + Rc, (double)dg[0]);
+            atomicAdd(I.rows + ny + Rc, (double)dg[1]);
+            atomicAdd(I.rows + 2 * ny + Rc, (double)dg[2]);
+            acc_n += (double)dg[3];
+            acc_phi += (double)dg[4];
+            acc_mom += (double)dg[5];
           }
         }
       }
@@ -547,13 +524,10 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kStepBlocksPerSM)
       sl = sl + 1 == D ? 0 : sl + 1;
     }
     cp_async_wait<0>();  // no copy may land after the warp moves on
-    if (DIAG) {
-      const double a = warp_sum(acc_n), b = warp_sum(acc_phi), m = warp_sum(acc_mom);
-      if (lane == 0) {
-        atomicAdd(I.sums + 0, a);
-        atomicAdd(I.sums + 1, b);
-        atomicAdd(I.sums + 2, m);
-      }
+    if (DIAG && lane == 0) {
+      atomicAdd(I.sums + 0, acc_n);
+      atomicAdd(I.sums + 1, acc_phi);
+      atomicAdd(I.sums + 2, acc_mom);
     }
   }
 }

@@ -58,9 +58,15 @@ __device__ __forceinline__ float stored(float v) {
   return H ? __half2float(__float2half_rn(v)) : v;
 }
 
+// Periodic wrap of a coordinate at most two periods outside [0, m) (every
+// caller offsets an in-range coordinate by one or two cells): compares and
+// adds instead of an integer division.
 __device__ __forceinline__ int wrap3(int v, int m) {
-  int r = v % m;
-  return r < 0 ? r + m : r;
+  if (v < 0) v += m;
+  if (v < 0) v += m;
+  if (v >= m) v -= m;
+  if (v >= m) v -= m;
+  return v;
 }
 
 __device__ __forceinline__ bool map_z(const Inst3& I, int z, int& zm) {

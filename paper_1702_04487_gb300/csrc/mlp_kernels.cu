@@ -291,11 +291,18 @@ size_t gemm_smem_bytes(int bn) {
 }
 
 cudaError_t launch_gemm(const GemmArgs& a, int members, cudaStream_t s) {
-  if (a.N <= 16) return launch_bn<16>(a, members, s);
-  if (a.N <= 32) return launch_bn<32>(a, members, s);
-  if (a.N <= 64) return launch_bn<64>(a, members, s);
-  if (a.N <= 128) return launch_bn<128>(a, members, s);
-  return launch_bn<256>(a, members, s);
+  // the narrowest tile that covers N, halved (down to 32 columns) while the
+  // grid has fewer than ~2 tiles per SM of a 152-SM part
+  int bn = a.N <= 16 ? 16 : a.N <= 32 ? 32 : a.N <= 64 ? 64 : a.N <= 128 ? 128 : 256;
+  const long long mt = (a.M + BM - 1) / BM;
+  while (bn > 32 && mt * ((a.N + bn - 1) / bn) * members < 304) bn /= 2;
+  switch (bn) {
+    case 16: return launch_bn<16>(a, members, s);
+    case 32: return launch_bn<32>(a, members, s);
+    case 64: return launch_bn<64>(a, members, s);
+    case 128: return launch_bn<128>(a, members, s);
+    default: return launch_bn<256>(a, members, s);
+  }
 }
 
 }  // namespace sg
