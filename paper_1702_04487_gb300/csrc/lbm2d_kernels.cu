@@ -212,7 +212,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kStepBlocksPerSM)
     const int cko = lane == 0 ? ckW : ckE;
     const bool drive_col = geom != GEOM_NOZZLE || (x >= I.cx0 && x < I.cx1);
     const float phis = I.phis, inv_phis = I.inv_phis, A4 = I.A4, kappa = I.kappa, hk = I.hk;
-    const float qf = I.q, omq = I.omq, inv_tphi = I.inv_tphi, gamma = I.gamma, inv2q = I.inv2q;
+    const float omq = I.omq, inv_tphi = I.inv_tphi, gamma = I.gamma, inv2q = I.inv2q;
+    const float qmt = I.q - I.inv_tphi;
     const float nu_air = I.nu_air, dnu = I.dnu, n0 = I.n0;
     const float Fd = drive_at(I, t);
     const float* __restrict__ fin = I.f[t & 1];
@@ -373,11 +374,11 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kStepBlocksPerSM)
           const float n = n0 + dn;
           const float mx = fr[1] - fr[3] + fr[5] - fr[6] - fr[7] + fr[8];
           const float my = fr[2] - fr[4] + fr[5] + fr[6] - fr[7] - fr[8];
-          const float inv_n = 1.0f / n;
+          const float inv_n = __frcp_rn(n);  // 1 / n, correctly rounded
           const float ux = (mx + 0.5f * Fx) * inv_n, uy = (my + 0.5f * Fy) * inv_n;
           const float u2 = ux * ux + uy * uy;
           if (!(u2 < 0.09f)) atomicOr(I.status, kStatusNumeric);
-          const float om = 1.0f / (0.5f + 3.0f * (nu_air + C * dnu));
+          const float om = __frcp_rn(0.5f + 3.0f * (nu_air + C * dnu));
           const float pref = 3.0f * (1.0f - 0.5f * om);
           // A_i - n0 = 3 (phi mu + n / 3) - n0 for i >= 1 (Eq. 6), on deviations
           const float p3 = dn + 3.0f * phi * mu;
@@ -392,10 +393,12 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kStepBlocksPerSM)
           // even part of the equilibrium and of the forcing term and differ
           // in the sign of the odd part: feq = E +- O, F = FE +- FO with
           // E = w (p3 + n (base + 4.5 cu^2)), O = 3 w n cu,
-          // FE = w pref (3 cu cF - uF), FO = w pref cF.
+          // FE = w pref (3 cu cF - uF), FO = w pref cF.  The collision
+          // f* = (1 - om) f + om feq + F then reads f*_i = (1 - om) f_i + A +- B
+          // with A = om E + FE and B = om O + FO.
           float fs[9];
-          float sum_eq = 0.0f, sum_F = 0.0f;
-          const float n3 = 3.0f * n;
+          float sumA = 0.0f;
+          const float omc = 1.0f - om, on3 = om * 3.0f * n;
 #pragma unroll
           for (int i = 1; i < 9; i++) {
             if (i == 3 || i == 4 || i == 7 || i == 8) continue;  // handled with its pair
@@ -404,17 +407,16 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kStepBlocksPerSM)
             const float ex = (float)cEX(i), ey = (float)cEY(i);
             const float cu = ex * ux + ey * uy;
             const float cF = ex * Fx + ey * Fy;
-            const float E = w * (p3 + n * (base + 4.5f * cu * cu));
-            const float O = (w * n3) * cu;
+            const float E = w * fmaf(n, fmaf(4.5f * cu, cu, base), p3);
             const float wp = w * pref;
-            const float FE = wp * (3.0f * cu * cF - uF);
-            const float FO = wp * cF;
-            sum_eq += 2.0f * E;
-            sum_F += 2.0f * FE;
-            fs[i] = fr[i] + om * ((E + O) - fr[i]) + (FE + FO);
-            fs[ib] = fr[ib] + om * ((E - O) - fr[ib]) + (FE - FO);
+            const float FE = wp * fmaf(3.0f * cu, cF, -uF);
+            const float A = fmaf(om, E, FE);
+            const float B = fmaf(w * on3, cu, wp * cF);
+            sumA += A;
+            fs[i] = fmaf(omc, fr[i], A + B);
+            fs[ib] = fmaf(omc, fr[ib], A - B);
           }
-          fs[0] = fr[0] + om * ((dn - sum_eq) - fr[0]) - sum_F;
+          fs[0] = fmaf(omc, fr[0], fmaf(om, dn, -2.0f * sumA));
 #pragma unroll
           for (int i = 1; i < 9; i++) cn[i - 1] = fs[i];
           // order parameter: Eq. 9-10 with the rest direction special; the
@@ -427,7 +429,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kStepBlocksPerSM)
             const float cu = (float)cEX(i) * ux + (float)cEY(i) * uy;
             const float ge = 0.5f * gmu + pq * cu;
             sum_ge += ge;
-            cn[7 + i] = qf * g2[i] + (ge - g2[i]) * inv_tphi;
+            cn[7 + i] = fmaf(qmt, g2[i], ge * inv_tphi);  // q g + (ge - g) / tau_phi
             on[1 + i] = omq * g2[i];
           }
           // rest direction: g0_0 = phi - sum_{i>=1} g0_i (Eq. 10 as a
