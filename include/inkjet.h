@@ -201,14 +201,14 @@ ij_status ij_kernel_timing(ij_handle h, int enable, double* total_ms, long long*
  * Launch-shape tuning (no counterpart in the paper).  The step kernel runs
  * one warp per work item: a strip of 28 columns (plus two halo columns on
  * each side) times a chunk of `chunk` rows of one lattice, with the
- * populations staged `prefetch` rows (1..4) ahead of use; blocks of 128
- * threads carry four items.  Every lattice of a handle is in the one bucket
- * of 128-thread blocks.
+ * populations staged `prefetch` rows (1..4) ahead of use; every block is
+ * one warp (32 threads), so a finished item frees its slot at once.  Every
+ * lattice of a handle is in the one bucket of 32-thread blocks.
  *
- * ij_tune      -- set chunk and prefetch (block_size: 128, or <= 0 for
+ * ij_tune      -- set chunk and prefetch (block_size: 32, or <= 0 for
  *                 every bucket).  Synchronises.
  * ij_autotune  -- time `reps` trial launches of every candidate (chunks
- *                 16..256, prefetch 1..4) on the current state and keep the
+ *                 8..256, prefetch 1..4) on the current state and keep the
  *                 fastest.  Trial launches leave the state and the time
  *                 unchanged.  Synchronises.
  * ij_get_tuning -- block size, chunk, prefetch and item count of bucket

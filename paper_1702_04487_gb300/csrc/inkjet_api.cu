@@ -330,9 +330,9 @@ void build_items(ij_handle h) {
     make_items(h->inst[k], k, b.chunk, h->items.data() + at, n);
   }
   b.count = (int)h->items.size();
-  // one block per four items: the block scheduler hands new blocks to SMs
-  // as they free up (measured faster than a persistent grid walking the
-  // list with a stride)
+  // one block per item: the block scheduler hands new blocks to SMs as
+  // they free up (measured faster than blocks of several items, which hold
+  // their slot until the slowest finishes, and than a persistent grid)
   b.grid = (b.count + kStepThreads / 32 - 1) / (kStepThreads / 32);
   h->buckets.push_back(b);
 }
@@ -925,7 +925,7 @@ ij_status ij_autotune(ij_handle h, int reps) {
   if (reps < 1) return fail(IJ_ERR_PARAM, "reps must be >= 1");
   if (h->poisoned) return fail(IJ_ERR_STATE, "handle is poisoned");
   if (h->is3d) return IJ_OK;  // the 3-D kernels have one fixed launch shape
-  static const int kChunks[] = {16, 32, 48, 64, 96, 128, 192, 256};
+  static const int kChunks[] = {8, 16, 24, 32, 48, 64, 128, 256};
   cudaEvent_t e0, e1;
   CUDA_TRY(cudaEventCreate(&e0));
   CUDA_TRY(cudaEventCreate(&e1));

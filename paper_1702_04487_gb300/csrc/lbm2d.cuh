@@ -49,8 +49,8 @@ struct Item {
   int inst, xs, nout, halo, y0, ch;
 };
 
-constexpr int kStepThreads = 128;  // 4 warps per block, one work item each
-constexpr int kStepBlocksPerSM = 4;  // resident blocks per SM (registers)
+constexpr int kStepThreads = 32;  // one warp per block, one work item each
+constexpr int kStepBlocksPerSM = 16;  // resident blocks per SM (registers: 128 each)
 constexpr int kMaxPrefetch = 4;    // rows staged ahead of use: 1 .. 4
 
 size_t step_smem_bytes(int nthreads, int prefetch);

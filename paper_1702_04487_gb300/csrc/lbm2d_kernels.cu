@@ -176,7 +176,7 @@ __device__ __forceinline__ int column_kind(const Inst& I, int x) {
 // to the other time buffer.  Every lane stages its own column's 14
 // populations of row R+P into the warp's shared-memory ring with cp.async,
 // P rows ahead of use, and reads back only what it staged itself.
-constexpr int kWarpsPerBlock = 4;
+constexpr int kWarpsPerBlock = kStepThreads / 32;
 constexpr int kRowFloats = 14 * 32;  // one staged row of a warp: g[5][32], then f[9][32]
 constexpr unsigned kFull = 0xffffffffu;
 
