@@ -115,13 +115,29 @@ __device__ __forceinline__ float drive_at(const Inst& I, long long t) {
   return 0.0f;
 }
 
-// Asynchronous 4-byte global -> shared copy (cp.async), issued only when
-// pred is set (a predicated instruction, no branch).
-__device__ __forceinline__ void cp_async4_if(float* dst, const float* src, bool pred) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+// Asynchronous 4-byte global -> shared copies (cp.async) of five / four
+// populations p, p + N, ... into shared addresses sa, sa + 128, ... (one
+// population row of a warp apart), issued only when pred is set: one
+// predicate and predicated instructions, no branch.
+__device__ __forceinline__ void cp5_if(unsigned sa, const float* p, int N, bool pred) {
   asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %2, 0;\n @p cp.async.ca.shared.global [%0], [%1], 4;\n}\n" ::"r"(sa),
-      "l"(src), "r"((int)pred)
+      "{\n .reg .pred p;\n setp.ne.b32 p, %6, 0;\n"
+      " @p cp.async.ca.shared.global [%0], [%1], 4;\n"
+      " @p cp.async.ca.shared.global [%0+128], [%2], 4;\n"
+      " @p cp.async.ca.shared.global [%0+256], [%3], 4;\n"
+      " @p cp.async.ca.shared.global [%0+384], [%4], 4;\n"
+      " @p cp.async.ca.shared.global [%0+512], [%5], 4;\n}\n" ::"r"(sa),
+      "l"(p), "l"(p + N), "l"(p + 2 * N), "l"(p + 3 * N), "l"(p + 4 * N), "r"((int)pred)
+      : "memory");
+}
+__device__ __forceinline__ void cp4_if(unsigned sa, const float* p, int N, bool pred) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %5, 0;\n"
+      " @p cp.async.ca.shared.global [%0], [%1], 4;\n"
+      " @p cp.async.ca.shared.global [%0+128], [%2], 4;\n"
+      " @p cp.async.ca.shared.global [%0+256], [%3], 4;\n"
+      " @p cp.async.ca.shared.global [%0+384], [%4], 4;\n}\n" ::"r"(sa),
+      "l"(p), "l"(p + N), "l"(p + 2 * N), "l"(p + 3 * N), "r"((int)pred)
       : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() {
@@ -188,6 +204,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kStepBlocksPerSM)
   extern __shared__ float4 smem4[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float* ring = reinterpret_cast<float*>(smem4) + warp * D * kRowFloats + lane;
+  const unsigned ring_sa = (unsigned)__cvta_generic_to_shared(ring);
   const long long t = *d_t + t_off;
 
   for (int item = blockIdx.x * kWarpsPerBlock + warp; item < n_items;
@@ -226,7 +243,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kStepBlocksPerSM)
     auto stage = [&](int r, int sp) {
       int ym;
       if (r <= y0 + ch + 2 && map_row_v(r, ny, bc, ym)) {  // uniform over the warp
-        float* d = ring + sp * kRowFloats;
+        const unsigned d = ring_sa + sp * (kRowFloats * 4);
         const bool own = row_kind(geom, ck, L, wt, ym) == 0;
         const bool fneed = own && col_lane && r >= y0 - 1 && r <= y0 + ch;
         // a solid edge lane has no populations of its own: the g of the
@@ -234,12 +251,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kStepBlocksPerSM)
         const bool outer = edge && !own && row_kind(geom, cko, L, wt, ym) == 0;
         const float* qg = gin + (ym * nx + x);
         const float* qf = outer ? gin + (ym * nx + xo) : fin + (ym * nx + x);
-#pragma unroll
-        for (int i = 0; i < 5; i++) cp_async4_if(d + i * 32, qg + i * N, own);
-#pragma unroll
-        for (int i = 0; i < 5; i++) cp_async4_if(d + (5 + i) * 32, qf + i * N, fneed || outer);
-#pragma unroll
-        for (int i = 5; i < 9; i++) cp_async4_if(d + (5 + i) * 32, qf + i * N, fneed);
+        cp5_if(d, qg, N, own);
+        cp5_if(d + 5 * 128, qf, N, fneed || outer);
+        cp4_if(d + 10 * 128, qf + 5 * N, N, fneed);
       }
       cp_async_commit();
     };
