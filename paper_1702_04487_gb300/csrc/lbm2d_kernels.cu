@@ -278,6 +278,13 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kStepBlocksPerSM)
     for (int i = 0; i < 12; i++) cB[i] = 0.f;
 #pragma unroll
     for (int i = 0; i < 6; i++) oB[i] = 0.f;
+    // the new row's values: lanes that do not collide keep the last ones
+    // (never read: their pulling neighbours bounce back)
+    float cn[12], on[6];
+#pragma unroll
+    for (int i = 0; i < 12; i++) cn[i] = 0.f;
+#pragma unroll
+    for (int i = 0; i < 6; i++) on[i] = 0.f;
     double acc_n = 0.0, acc_phi = 0.0, acc_mom = 0.0;
     int sl = 0;  // ring slot of row R
 
@@ -354,7 +361,6 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kStepBlocksPerSM)
       }
       // ---- collision of row Rc = R-2 into cn / on
       const int Rc = R - 2;
-      float cn[12], on[6];
       {
         const float nW = __shfl_up_sync(kFull, pe0, 1), nE = __shfl_down_sync(kFull, pe0, 1);
         const float cW = __shfl_up_sync(kFull, pe1, 1), cE = __shfl_down_sync(kFull, pe1, 1);
@@ -460,11 +466,6 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kStepBlocksPerSM)
             dg[4] = phi;
             dg[5] = n * uy;
           }
-        } else {
-#pragma unroll
-          for (int i = 0; i < 12; i++) cn[i] = 0.f;
-#pragma unroll
-          for (int i = 0; i < 6; i++) on[i] = 0.f;
         }
         if (DIAG && k >= 4 && Rc >= y0 && Rc < y0 + ch) {
           // the strip's 28 cells of the row are summed in FP32, every

@@ -169,146 +169,176 @@ __device__ __forceinline__ float drive3(const Inst3& I, long long t) {
   return 0.0f;
 }
 
-__device__ __forceinline__ double warp_sum3(double v) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  return v;
-}
-
 // ---------------------------------------------------------------------------
+// Collision of the planes [zfirst, zlast) of a 32 x 4 column tile; the block
+// marches up z and keeps phi of planes z-1, z, z+1 of the tile (with a
+// one-cell halo) in shared memory, so that the D3Q19 stencil of a fluid cell
+// away from walls reads shared memory only.
+constexpr int kZChunk = 8;
+constexpr int kTX = 32, kTY = 4;
+
 template <bool H, bool DIAG>
 __global__ void __launch_bounds__(128) collide3_kernel(const Inst3* __restrict__ insts, int index,
                                                        const long long* __restrict__ d_t,
                                                        int t_off) {
+  __shared__ float tile[3][kTY + 2][kTX + 2];
+  __shared__ float red[4][6];
   const Inst3& I = insts[index];
   // a lattice whose numeric flag is set is frozen; one read per block keeps
-  // the decision uniform over the block's barrier below
+  // the decision uniform over the block's barriers below
   const bool lead = threadIdx.x == 0 && threadIdx.y == 0;
   if (__syncthreads_or(lead && (*(volatile const unsigned*)I.status & kStatusNumeric))) return;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int tid = threadIdx.y * kTX + threadIdx.x;
+  const int x = blockIdx.x * kTX + threadIdx.x;
+  const int y = blockIdx.y * kTY + threadIdx.y;
   // zero-gradient ends: the planes z = -1 and z = nz of the extended lattice
   // collide too (their populations are the edge plane's, their stencils
   // their own), so that the streaming can pull from them
-  const int z = (int)blockIdx.z - (I.bc == BC_ZG ? 1 : 0);
-  int zm = z;
-  const bool inz = map_z(I, z, zm);
-  const bool inr = x < I.nx && y < I.ny && inz;
+  const int zoff = I.bc == BC_ZG ? 1 : 0;
+  const int zfirst = (int)blockIdx.z * kZChunk - zoff;
+  const int zlast = min(zfirst + kZChunk, I.nz + zoff);
   const size_t N = (size_t)I.nx * I.ny * I.nz, NP = (size_t)I.nx * I.ny * (I.nz + 2);
-  const size_t c = inr ? cell3(I, x, y, zm) : 0;
-  const size_t cp = inr ? ((size_t)(z + 1) * I.ny + y) * I.nx + x : 0;  // post-collision plane
-  const bool fluid = inr && geom_kind3(I, x, y, zm) == 0;
-  const bool owned = z >= 0 && z < I.nz;  // diagnostics count in-domain cells only
   const long long t = *d_t + t_off;
-  double dw = 0.0, dm = 0.0, dp = 0.0, an = 0.0, aphi = 0.0, amom = 0.0;
-  if (fluid) {
-    float fr[19], gr[7];
-#pragma unroll
-    for (int i = 0; i < 19; i++) fr[i] = ldS<H>(I.f, i * N + c);
-    gr[0] = I.g0[c];
-#pragma unroll
-    for (int i = 1; i < 7; i++) gr[i] = ldS<H>(I.g, (i - 1) * N + c);
-    const float phi = gr[0] + gr[1] + gr[2] + gr[3] + gr[4] + gr[5] + gr[6];
-    // D3Q19 stencils on phi with wetting ghosts
-    const bool ns = near_solid3(I, x, y, zm) || !owned;
-    float lap = 0.0f, gx = 0.0f, gy = 0.0f, gz = 0.0f;
-#pragma unroll
-    for (int i = 1; i < 19; i++) {
-      const int xn = x + ex3(i), yn = y + ey3(i), zn = z + ez3(i);
-      float pn;
-      if (ns && kind_at3(I, xn, yn, zn) != 0)
-        pn = ghost3(I, xn, yn, zn);
-      else
-        pn = phi_at3(I, xn, yn, zn);
-      lap += 6.0f * w3(i) * (pn - phi);
-      gx += 3.0f * w3(i) * (float)ex3(i) * pn;
-      gy += 3.0f * w3(i) * (float)ey3(i) * pn;
-      gz += 3.0f * w3(i) * (float)ez3(i) * pn;
+  const float drive = drive3(I, t);
+  const bool inxy = x < I.nx && y < I.ny;
+  // phi of plane zz (extended index) into its ring slot, with the tile's halo
+  auto load_plane = [&](int zz) {
+    const int slot = ((zz % 3) + 3) % 3;
+    int zm = 0;
+    const bool ok = map_z(I, zz, zm);
+    for (int idx = tid; idx < (kTY + 2) * (kTX + 2); idx += kTX * kTY) {
+      const int lx = idx % (kTX + 2), ly = idx / (kTX + 2);
+      int gx = ((int)blockIdx.x * kTX + lx - 1) % I.nx, gy = ((int)blockIdx.y * kTY + ly - 1) % I.ny;
+      if (gx < 0) gx += I.nx;
+      if (gy < 0) gy += I.ny;
+      tile[slot][ly][lx] = ok ? I.phi[cell3(I, gx, gy, zm)] : 0.0f;
     }
-    const float mu = I.A4 * phi * ((phi - I.phis) * (phi + I.phis)) - I.kappa * lap;
-    float C = fminf(fmaxf(0.5f * (phi * I.inv_phis + 1.0f), 0.0f), 1.0f);
-    const bool dreg = I.geom != GEOM_NOZZLE || (zm < I.L && rr2(I, x, y) < I.R2);
-    const float Fb = dreg ? drive3(I, t) * C : 0.0f;
-    const float Fx = mu * gx, Fy = mu * gy, Fz = mu * gz + Fb;
-    float dn = 0.0f, mx = 0.0f, my = 0.0f, mz = 0.0f;
-#pragma unroll
-    for (int i = 0; i < 19; i++) {
-      dn += fr[i];
-      mx += (float)ex3(i) * fr[i];
-      my += (float)ey3(i) * fr[i];
-      mz += (float)ez3(i) * fr[i];
-    }
-    const float n = I.n0 + dn, inv_n = 1.0f / n;
-    const float ux = (mx + 0.5f * Fx) * inv_n, uy = (my + 0.5f * Fy) * inv_n,
-                uz = (mz + 0.5f * Fz) * inv_n;
-    const float u2 = ux * ux + uy * uy + uz * uz;
-    if (!(u2 < 0.09f)) atomicOr(I.status, kStatusNumeric);
-    const float om = 1.0f / (0.5f + 3.0f * (I.nu_air + C * I.dnu));
-    const float pref = 3.0f * (1.0f - 0.5f * om);
-    const float p3 = dn + 3.0f * phi * mu;  // A_i - n0 for i >= 1
-    const float uF = ux * Fx + uy * Fy + uz * Fz, base = -1.5f * u2, n3 = 3.0f * n;
-    float fs[19], sum_eq = 0.0f, sum_F = 0.0f;
-    // opposite pairs share the even parts (see the 2-D kernel)
-#pragma unroll
-    for (int i = 1; i < 19; i++) {
-      if (opp3(i) < i) continue;
-      const int ib = opp3(i);
-      const float w = w3(i);
-      const float cu = (float)ex3(i) * ux + (float)ey3(i) * uy + (float)ez3(i) * uz;
-      const float cF = (float)ex3(i) * Fx + (float)ey3(i) * Fy + (float)ez3(i) * Fz;
-      const float E = w * (p3 + n * (base + 4.5f * cu * cu)), O = (w * n3) * cu;
-      const float wp = w * pref, FE = wp * (3.0f * cu * cF - uF), FO = wp * cF;
-      sum_eq += 2.0f * E;
-      sum_F += 2.0f * FE;
-      fs[i] = fr[i] + om * ((E + O) - fr[i]) + (FE + FO);
-      fs[ib] = fr[ib] + om * ((E - O) - fr[ib]) + (FE - FO);
-    }
-    fs[0] = fr[0] + om * ((dn - sum_eq) - fr[0]) - sum_F;
-#pragma unroll
-    for (int i = 0; i < 19; i++) stS<H>(I.fp, i * NP + cp, fs[i]);
-    // order parameter: D3Q7, rest direction special
-    const float gmu = I.gamma * mu, pq = phi * I.inv2q;
-    float sum_ge = 0.0f, sum_g = 0.0f;
-#pragma unroll
-    for (int i = 1; i < 7; i++) {
-      const float cu = (float)ex3(i) * ux + (float)ey3(i) * uy + (float)ez3(i) * uz;
-      const float ge = 0.5f * gmu + pq * cu;
-      sum_ge += ge;
-      sum_g += gr[i];
-      stS<H>(I.gp, (i - 1) * NP + cp, I.q * gr[i] + (ge - gr[i]) * I.inv_tphi);
-    }
-    I.g0p[cp] = gr[0] + (sum_g - sum_ge) * I.inv_tphi;
-    if (DIAG && owned) {
-      const float e = fminf(fmaxf(phi * I.inv_phis, 0.0f), 1.0f);
-      dw = e;
-      dm = (double)e * n;
-      dp = dm * uz;
-      an = n;
-      aphi = phi;
-      amom = (double)n * uz;
-    }
-  }
-  if (DIAG && (I.bc != BC_ZG || (blockIdx.z >= 1 && blockIdx.z <= (unsigned)I.nz))) {
-    __shared__ double red[4][6];
-    double v[6] = {dw, dm, dp, an, aphi, amom};
-    const int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31;
-    const int warp = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
-#pragma unroll
-    for (int k = 0; k < 6; k++) v[k] = warp_sum3(v[k]);
-    if (lane == 0)
-#pragma unroll
-      for (int k = 0; k < 6; k++) red[warp][k] = v[k];
+  };
+  load_plane(zfirst - 1);
+  load_plane(zfirst);
+  for (int z = zfirst; z < zlast; z++) {
+    load_plane(z + 1);
     __syncthreads();
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
-      double s[6] = {0, 0, 0, 0, 0, 0};
-      for (int wq = 0; wq < 4; wq++)
-        for (int k = 0; k < 6; k++) s[k] += red[wq][k];
-      atomicAdd(I.rows + z, s[0]);
-      atomicAdd(I.rows + I.nz + z, s[1]);
-      atomicAdd(I.rows + 2 * I.nz + z, s[2]);
-      atomicAdd(I.sums + 0, s[3]);
-      atomicAdd(I.sums + 1, s[4]);
-      atomicAdd(I.sums + 2, s[5]);
+    int zm = z;
+    const bool inz = map_z(I, z, zm);
+    const bool inr = inxy && inz;
+    const size_t c = inr ? cell3(I, x, y, zm) : 0;
+    const size_t cp = inr ? ((size_t)(z + 1) * I.ny + y) * I.nx + x : 0;  // post-collision plane
+    const bool fluid = inr && geom_kind3(I, x, y, zm) == 0;
+    const bool owned = z >= 0 && z < I.nz;  // diagnostics count in-domain cells only
+    float dg[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (fluid) {
+      float fr[19], gr[7];
+#pragma unroll
+      for (int i = 0; i < 19; i++) fr[i] = ldS<H>(I.f, i * N + c);
+      gr[0] = I.g0[c];
+#pragma unroll
+      for (int i = 1; i < 7; i++) gr[i] = ldS<H>(I.g, (i - 1) * N + c);
+      const float phi = gr[0] + gr[1] + gr[2] + gr[3] + gr[4] + gr[5] + gr[6];
+      // D3Q19 stencils on phi with wetting ghosts
+      const bool ns = near_solid3(I, x, y, zm) || !owned;
+      float lap = 0.0f, gx = 0.0f, gy = 0.0f, gz = 0.0f;
+#pragma unroll
+      for (int i = 1; i < 19; i++) {
+        const int xn = x + ex3(i), yn = y + ey3(i), zn = z + ez3(i);
+        float pn;
+        if (ns && kind_at3(I, xn, yn, zn) != 0)
+          pn = ghost3(I, xn, yn, zn);
+        else
+          pn = tile[((zn % 3) + 3) % 3][threadIdx.y + 1 + ey3(i)][threadIdx.x + 1 + ex3(i)];
+        lap += 6.0f * w3(i) * (pn - phi);
+        gx += 3.0f * w3(i) * (float)ex3(i) * pn;
+        gy += 3.0f * w3(i) * (float)ey3(i) * pn;
+        gz += 3.0f * w3(i) * (float)ez3(i) * pn;
+      }
+      const float mu = I.A4 * phi * ((phi - I.phis) * (phi + I.phis)) - I.kappa * lap;
+      float C = fminf(fmaxf(0.5f * (phi * I.inv_phis + 1.0f), 0.0f), 1.0f);
+      const bool dreg = I.geom != GEOM_NOZZLE || (zm < I.L && rr2(I, x, y) < I.R2);
+      const float Fb = dreg ? drive * C : 0.0f;
+      const float Fx = mu * gx, Fy = mu * gy, Fz = mu * gz + Fb;
+      float dn = 0.0f, mx = 0.0f, my = 0.0f, mz = 0.0f;
+#pragma unroll
+      for (int i = 0; i < 19; i++) {
+        dn += fr[i];
+        mx += (float)ex3(i) * fr[i];
+        my += (float)ey3(i) * fr[i];
+        mz += (float)ez3(i) * fr[i];
+      }
+      const float n = I.n0 + dn, inv_n = __frcp_rn(n);
+      const float ux = (mx + 0.5f * Fx) * inv_n, uy = (my + 0.5f * Fy) * inv_n,
+                  uz = (mz + 0.5f * Fz) * inv_n;
+      const float u2 = ux * ux + uy * uy + uz * uz;
+      if (!(u2 < 0.09f)) atomicOr(I.status, kStatusNumeric);
+      const float om = __frcp_rn(0.5f + 3.0f * (I.nu_air + C * I.dnu));
+      const float pref = 3.0f * (1.0f - 0.5f * om);
+      const float p3 = dn + 3.0f * phi * mu;  // A_i - n0 for i >= 1
+      const float uF = ux * Fx + uy * Fy + uz * Fz, base = -1.5f * u2;
+      const float n3 = 3.0f * n;
+      float fs[19], sum_eq = 0.0f, sum_F = 0.0f;
+      // opposite pairs share the even parts (see the 2-D kernel)
+#pragma unroll
+      for (int i = 1; i < 19; i++) {
+        if (opp3(i) < i) continue;
+        const int ib = opp3(i);
+        const float w = w3(i);
+        const float cu = (float)ex3(i) * ux + (float)ey3(i) * uy + (float)ez3(i) * uz;
+        const float cF = (float)ex3(i) * Fx + (float)ey3(i) * Fy + (float)ez3(i) * Fz;
+        const float E = w * (p3 + n * (base + 4.5f * cu * cu)), O = (w * n3) * cu;
+        const float wp = w * pref, FE = wp * (3.0f * cu * cF - uF), FO = wp * cF;
+        sum_eq += 2.0f * E;
+        sum_F += 2.0f * FE;
+        fs[i] = fr[i] + om * ((E + O) - fr[i]) + (FE + FO);
+        fs[ib] = fr[ib] + om * ((E - O) - fr[ib]) + (FE - FO);
+      }
+      fs[0] = fr[0] + om * ((dn - sum_eq) - fr[0]) - sum_F;
+#pragma unroll
+      for (int i = 0; i < 19; i++) stS<H>(I.fp, i * NP + cp, fs[i]);
+      // order parameter: D3Q7, rest direction special
+      const float gmu = I.gamma * mu, pq = phi * I.inv2q;
+      float sum_ge = 0.0f, sum_g = 0.0f;
+#pragma unroll
+      for (int i = 1; i < 7; i++) {
+        const float cu = (float)ex3(i) * ux + (float)ey3(i) * uy + (float)ez3(i) * uz;
+        const float ge = 0.5f * gmu + pq * cu;
+        sum_ge += ge;
+        sum_g += gr[i];
+        stS<H>(I.gp, (i - 1) * NP + cp, I.q * gr[i] + (ge - gr[i]) * I.inv_tphi);
+      }
+      I.g0p[cp] = gr[0] + (sum_g - sum_ge) * I.inv_tphi;
+      if (DIAG && owned) {
+        const float e = fminf(fmaxf(phi * I.inv_phis, 0.0f), 1.0f);
+        dg[0] = e;
+        dg[1] = e * n;
+        dg[2] = dg[1] * uz;
+        dg[3] = n;
+        dg[4] = phi;
+        dg[5] = n * uz;
+      }
     }
+    if (DIAG && owned) {  // uniform over the block: one plane
+      // a warp's 32 cells summed in FP32, the warps and every total in FP64
+      const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < 6; k++) dg[k] += __shfl_down_sync(0xffffffffu, dg[k], o);
+      if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < 6; k++) red[warp][k] = dg[k];
+      __syncthreads();
+      if (tid == 0) {
+        double s[6] = {0, 0, 0, 0, 0, 0};
+        for (int wq = 0; wq < 4; wq++)
+          for (int k = 0; k < 6; k++) s[k] += (double)red[wq][k];
+        atomicAdd(I.rows + z, s[0]);
+        atomicAdd(I.rows + I.nz + z, s[1]);
+        atomicAdd(I.rows + 2 * I.nz + z, s[2]);
+        atomicAdd(I.sums + 0, s[3]);
+        atomicAdd(I.sums + 1, s[4]);
+        atomicAdd(I.sums + 2, s[5]);
+      }
+    }
+    __syncthreads();  // the slot of plane z-1 is refilled with plane z+2 next
   }
 }
 
@@ -518,7 +548,8 @@ __global__ void phi3_kernel(const Inst3* __restrict__ insts, int index, float* o
 
 dim3 grid3(const Inst3& h) { return dim3((h.nx + 31) / 32, (h.ny + 3) / 4, h.nz); }
 dim3 grid3c(const Inst3& h) {
-  return dim3((h.nx + 31) / 32, (h.ny + 3) / 4, h.nz + (h.bc == BC_ZG ? 2 : 0));
+  return dim3((h.nx + kTX - 1) / kTX, (h.ny + kTY - 1) / kTY,
+              (h.nz + (h.bc == BC_ZG ? 2 : 0) + kZChunk - 1) / kZChunk);
 }
 
 }  // namespace
