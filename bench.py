@@ -82,6 +82,23 @@ def workload(name, rank=0):
     return ps, desc
 
 
+def max_over_ranks(x, world, device):
+    """The largest of every rank's x (the slowest rank sets the job's time)."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(cells_per_rank, steps, world, seconds):
+    """Whole-job throughput: every rank advanced cells_per_rank cells by
+    `steps` steps in the slowest rank's `seconds` (weak scaling)."""
+    return cells_per_rank * steps * world / seconds / 1e6
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -256,11 +273,8 @@ def run_native(args):
     clk = clocks.stop()
     obs, _ = inkjet.ij_observe(h, 0, phi=False)
     inkjet.ij_destroy(h)
-    t = torch.tensor([ms], device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = cells * args.steps * world / (ms_max / 1e3) / 1e6
+    ms_max = max_over_ranks(ms, world, "cuda")
+    value = job_mlups(cells, args.steps, world, ms_max / 1e3)
 
     # ---- end to end through the public API, host buffers
     import numpy as np
@@ -278,10 +292,7 @@ def run_native(args):
     barrier()
     e2e_s = time.perf_counter() - t0
     inkjet.ij_destroy(h2)
-    te = torch.tensor([e2e_s], device="cuda")
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = cells * args.steps * world / float(te.item()) / 1e6
+    e2e_value = job_mlups(cells, args.steps, world, max_over_ranks(e2e_s, world, "cuda"))
     h2d = len(params) * inkjet.C.sizeof(inkjet.ij_params)
     d2h = sum(ph.nbytes for ph in phis) + len(params) * inkjet.C.sizeof(inkjet.ij_obs)
 
