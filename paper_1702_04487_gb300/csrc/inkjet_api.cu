@@ -307,8 +307,6 @@ Inst3 derive3(const ij_params& p) {
   return I;
 }
 
-// Block size of a lattice: one strip of round_up(nx, 32) threads when nx
-// fits in 256 columns, else overlapping strips of 256 threads.
 // Every lattice runs in the one bucket of kStepThreads-thread blocks (one
 // warp per work item).
 int block_size_for(const Inst&) { return kStepThreads; }
@@ -323,12 +321,21 @@ void build_items(ij_handle h) {
       b.chunk = o.chunk;
       b.prefetch = o.prefetch;
     }
-  for (int k = 0; k < h->n_inst; k++) {
-    const int n = items_per_lattice(h->inst[k], b.chunk);
-    const size_t at = h->items.size();
-    h->items.resize(at + n);
-    make_items(h->inst[k], k, b.chunk, h->items.data() + at, n);
-  }
+  // The last quarter of every lattice's rows is cut into chunks a quarter
+  // as long, and those items go last: the final wave of blocks is made of
+  // short items, so SMs run out of work together.
+  const int tail_chunk = std::max(4, b.chunk / 4);
+  for (int pass = 0; pass < 2; pass++)
+    for (int k = 0; k < h->n_inst; k++) {
+      const Inst& I = h->inst[k];
+      const int split = I.ny - I.ny / 4;
+      const int ya = pass == 0 ? 0 : split, yb = pass == 0 ? split : I.ny;
+      const int ch = pass == 0 ? b.chunk : tail_chunk;
+      const int n = items_per_range(I, ch, ya, yb);
+      const size_t at = h->items.size();
+      h->items.resize(at + n);
+      make_items_range(I, k, ch, ya, yb, h->items.data() + at, n);
+    }
   b.count = (int)h->items.size();
   // one block per item: the block scheduler hands new blocks to SMs as
   // they free up (measured faster than blocks of several items, which hold

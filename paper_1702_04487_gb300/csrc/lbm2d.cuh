@@ -59,6 +59,9 @@ cudaError_t set_step_smem_limit();
 // (at most cap); returns the count, or -1 when cap is too small.
 int make_items(const Inst& I, int k, int chunk, Item* out, int cap);
 int items_per_lattice(const Inst& I, int chunk);
+// The same for rows ya .. yb-1 only.
+int make_items_range(const Inst& I, int k, int chunk, int ya, int yb, Item* out, int cap);
+int items_per_range(const Inst& I, int chunk, int ya, int yb);
 
 // host helpers of inkjet_api.cu
 ij_status validate_params(const ij_params& p, int k);

@@ -915,11 +915,11 @@ cudaError_t set_step_smem_limit() {
   return e;
 }
 
-int make_items(const Inst& I, int k, int chunk, Item* out, int cap) {
+int make_items_range(const Inst& I, int k, int chunk, int ya, int yb, Item* out, int cap) {
   constexpr int halo = 2, W = 32 - 2 * halo;  // 28 written columns per strip
   const int nstrip = (I.nx + W - 1) / W;
   int n = 0;
-  for (int y0 = 0; y0 < I.ny; y0 += chunk)
+  for (int y0 = ya; y0 < yb; y0 += chunk)
     for (int s = 0; s < nstrip; s++) {
       if (n >= cap) return -1;
       Item& it = out[n++];
@@ -928,13 +928,19 @@ int make_items(const Inst& I, int k, int chunk, Item* out, int cap) {
       it.nout = I.nx - s * W < W ? I.nx - s * W : W;
       it.halo = halo;
       it.y0 = y0;
-      it.ch = I.ny - y0 < chunk ? I.ny - y0 : chunk;
+      it.ch = yb - y0 < chunk ? yb - y0 : chunk;
     }
   return n;
 }
 
-int items_per_lattice(const Inst& I, int chunk) {
-  return ((I.nx + 27) / 28) * ((I.ny + chunk - 1) / chunk);
+int make_items(const Inst& I, int k, int chunk, Item* out, int cap) {
+  return make_items_range(I, k, chunk, 0, I.ny, out, cap);
 }
+
+int items_per_range(const Inst& I, int chunk, int ya, int yb) {
+  return yb > ya ? ((I.nx + 27) / 28) * ((yb - ya + chunk - 1) / chunk) : 0;
+}
+
+int items_per_lattice(const Inst& I, int chunk) { return items_per_range(I, chunk, 0, I.ny); }
 
 }  // namespace ij
