@@ -8,11 +8,16 @@
 // contiguous, "K-major").  A CTA of 128 threads owns a 128 x BN tile of C,
 // BN in {16, 32, 64, 128, 256}.  K advances in slices of 64 (128 bytes of
 // BF16, one row of a 128-byte swizzle atom), double-buffered in shared
-// memory: cp.async fills slice k+1 while the tensor core multiplies slice k.
-// One thread issues the four K=16 MMAs of a slice and commits them to the
-// slice's mbarrier; the loaders wait on that barrier before reusing the
-// buffer.  The epilogue reads the accumulator with tcgen05.ld (warp w owns
-// tensor-memory lanes 32w..32w+31, i.e. rows 32w..32w+31 of the tile).
+// memory.  One thread drives the pipeline: it loads a slice of A and of B
+// with the tensor memory accelerator (cp.async.bulk.tensor, 128-byte
+// swizzle written by the copy itself, completion counted in bytes on the
+// slice's load mbarrier), issues the four K=16 MMAs of the slice once it
+// has landed and commits them to the slice's MMA mbarrier, which frees the
+// buffer for the slice after next; the load of slice k+1 runs while the
+// tensor core multiplies slice k.  The epilogue reads the accumulator with
+// tcgen05.ld (warp w owns tensor-memory lanes 32w..32w+31, i.e. rows
+// 32w..32w+31 of the tile).
+#include <cuda.h>
 #include <math.h>
 
 #include "mlp.cuh"
@@ -27,20 +32,6 @@ constexpr int kWaitLimit = 1 << 22;  // try_wait rounds before giving up
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-// 16-byte asynchronous copy global -> shared; zero fill when !valid.
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src),
-               "r"(valid ? 16 : 0)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.wait_all;\n" ::: "memory");
-}
-// make this thread's shared-memory writes visible to the tensor core
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
 }
 
 __device__ __forceinline__ void mbar_init(uint32_t bar, int count) {
@@ -137,26 +128,27 @@ __host__ __device__ constexpr int tmem_cols() {
   return BN < 32 ? 32 : BN;
 }
 
-// Copy one 64-wide K slice of `rows` rows (row-major, leading dimension ld)
-// into a 128-byte-swizzled tile: 16-byte chunk c of row r lands at
-// r * 128 + ((c ^ (r % 8)) * 16).  Rows >= nrows and columns >= K are zero.
-template <int ROWS>
-__device__ __forceinline__ void load_tile(uint32_t tile, const bf16* src, int ld, int row0,
-                                          int nrows, int k0, int K, int tid) {
-#pragma unroll
-  for (int i = 0; i < (ROWS * 8 + kThreads - 1) / kThreads; i++) {
-    const int idx = tid + i * kThreads;
-    if (idx >= ROWS * 8) break;
-    const int r = idx >> 3, c = idx & 7;
-    const int gr = row0 + r, gk = k0 + c * 8;
-    const bool valid = gr < nrows && gk < K;
-    const bf16* p = valid ? src + (size_t)gr * ld + gk : src;
-    cp_async16(tile + r * 128 + ((c ^ (r & 7)) << 4), p, valid);
-  }
+// Arm the load barrier for `bytes` of asynchronous copies (one arrival).
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+// One box of a 3-D tensor map (x = K offset, y = row, z = member) into
+// shared memory; completion is counted on `bar`.
+__device__ __forceinline__ void tma_load3(uint32_t dst, const CUtensorMap* map, int x, int y, int z,
+                                          uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
 }
 
 template <int BN>
-__global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const GemmArgs a) {
+__global__ void __launch_bounds__(kThreads, 1)
+    gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                const GemmArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -164,18 +156,18 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const GemmArgs a) {
   constexpr int kStage = stage_bytes<BN>();
   constexpr uint32_t kCols = tmem_cols<BN>();
   constexpr uint32_t kIdesc = idesc_bf16(BM, BN);
+  // bars[0..1]: loads of buffers 0 / 1 landed; bars[2..3]: their MMAs done
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * kStage);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 4);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int z = blockIdx.z;
-  const bf16* A = a.A + z * a.sA;
-  const bf16* B = a.B + z * a.sB;
   const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  const int za = a.sA ? z : 0, zb = a.sB ? z : 0;  // a zero stride shares one operand
 
   if (tid == 0) {
-    mbar_init(smem_u32(&bars[0]), 1);
-    mbar_init(smem_u32(&bars[1]), 1);
+#pragma unroll
+    for (int i = 0; i < 4; i++) mbar_init(smem_u32(&bars[i]), 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   if (warp == 0) {
@@ -192,34 +184,37 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const GemmArgs a) {
 
   const int nk = (a.K + BK - 1) / BK;
   bool ok = true;
-  int issued = 0;  // slices whose MMAs were committed
-  for (int kt = 0; kt < nk; kt++) {
-    const int s = kt & 1;
-    // the MMAs of slice kt-2 read this buffer: wait for their commit
-    if (kt >= 2) ok = __syncthreads_and(mbar_wait(smem_u32(&bars[s]), ((kt - 2) >> 1) & 1));
-    if (!ok) break;
-    const uint32_t ta = smem_u32(smem + s * kStage), tb = ta + kA;
-    load_tile<BM>(ta, A, a.lda, m0, a.M, kt * BK, a.K, tid);
-    load_tile<BN>(tb, B, a.ldb, n0, a.N, kt * BK, a.K, tid);
-    cp_async_wait_all();
-    fence_proxy_async();
-    __syncthreads();
-    if (tid == 0) {
+  if (tid == 0) {
+    int issued = 0;  // slices whose MMAs were committed
+    for (int kt = 0; kt < nk && ok; kt++) {
+      const int s = kt & 1;
+      // the MMAs of slice kt-2 read this buffer: wait for their commit
+      if (kt >= 2 && !mbar_wait(smem_u32(&bars[2 + s]), ((kt - 2) >> 1) & 1)) {
+        ok = false;
+        break;
+      }
+      const uint32_t ta = smem_u32(smem + s * kStage), tb = ta + kA;
+      mbar_expect_tx(smem_u32(&bars[s]), (uint32_t)kStage);
+      tma_load3(ta, &tmA, kt * BK, m0, za, smem_u32(&bars[s]));
+      tma_load3(tb, &tmB, kt * BK, n0, zb, smem_u32(&bars[s]));
+      if (!mbar_wait(smem_u32(&bars[s]), (kt >> 1) & 1)) {
+        ok = false;
+        break;
+      }
       tc_fence_after();
 #pragma unroll
       for (int k = 0; k < BK / 16; k++)
         mma_bf16(tmem, sw128_desc(ta + 32 * k), sw128_desc(tb + 32 * k), kIdesc,
                  (kt > 0 || k > 0) ? 1u : 0u);
-      mma_commit(smem_u32(&bars[s]));
+      mma_commit(smem_u32(&bars[2 + s]));
+      issued = kt + 1;
     }
-    issued = kt + 1;
+    // every committed slice must have completed before the accumulator is
+    // read or the tensor memory is released: the last commit of each buffer
+    for (int kt = issued > 2 ? issued - 2 : 0; kt < issued; kt++)
+      ok = mbar_wait(smem_u32(&bars[2 + (kt & 1)]), (kt >> 1) & 1) && ok;
   }
-  // every committed slice must have completed before the accumulator is read
-  // or the tensor memory is released: wait for the last commit of each buffer
-  bool done = true;
-  for (int kt = issued > 2 ? issued - 2 : 0; kt < issued; kt++)
-    done = mbar_wait(smem_u32(&bars[kt & 1]), (kt >> 1) & 1) && done;
-  ok = __syncthreads_and(ok && done);
+  ok = __syncthreads_and(ok);
   tc_fence_after();
 
   if (ok) {
@@ -269,9 +264,54 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const GemmArgs a) {
   }
 }
 
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// The driver's tensor-map encoder, looked up once through the runtime (no
+// link against the driver library).
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static bool looked = false;
+  if (!looked) {
+    looked = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// 3-D tensor map of a BF16 operand: K (contiguous) x rows (leading dimension
+// ld) x layers (stride layer, or one layer), boxes of 64 x box_rows x 1 in
+// the 128-byte swizzle; out-of-range elements read as zero.
+cudaError_t make_map(CUtensorMap* m, const bf16* base, int K, int rows, int ld,
+                     long long layer, int layers, int box_rows) {
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) return cudaErrorNotSupported;
+  const cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)layers};
+  const cuuint64_t strides[2] = {(cuuint64_t)ld * 2,
+                                 (cuuint64_t)(layers > 1 ? layer : (long long)ld * rows) * 2};
+  const cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<bf16*>(base), dims,
+                         strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 template <int BN>
 cudaError_t launch_bn(const GemmArgs& a, int members, cudaStream_t s) {
   const size_t smem = gemm_smem_bytes(BN);
+  CUtensorMap ma, mb;
+  cudaError_t e0 = make_map(&ma, a.A, a.K, a.M, a.lda, a.sA, a.sA ? members : 1, BM);
+  if (e0 == cudaSuccess) e0 = make_map(&mb, a.B, a.K, a.N, a.ldb, a.sB, a.sB ? members : 1, BN);
+  if (e0 != cudaSuccess) return e0;
   static bool attr = false;
   if (!attr) {
     cudaError_t e =
@@ -280,7 +320,7 @@ cudaError_t launch_bn(const GemmArgs& a, int members, cudaStream_t s) {
     attr = true;
   }
   dim3 grid((a.M + BM - 1) / BM, (a.N + BN - 1) / BN, members);
-  gemm_kernel<BN><<<grid, kThreads, smem, s>>>(a);
+  gemm_kernel<BN><<<grid, kThreads, smem, s>>>(ma, mb, a);
   return cudaGetLastError();
 }
 
