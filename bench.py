@@ -24,9 +24,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MLUPS & %HBM peak, plain vs batched/FP16-store LBM; surrogate speedup at err"
 # Algorithmic bytes per lattice update: the stored populations read once and
-# written once.  2-D: (9 + 5) FP32.  3-D: (19 + 7) FP32, or with FP16
-# storage 19 + 6 FP16 and g_0 in FP32.
-BYTES_PER_LUP = {"2d": 112, "3d32": 208, "3d16": 108}
+# written once.  2-D: (9 + 5) FP32, or with FP16 storage 9 + 4 FP16 and g_0
+# in FP32.  3-D: (19 + 7) FP32, or 19 + 6 FP16 and g_0 in FP32.
+BYTES_PER_LUP = {"2d": 112, "2d16": 60, "3d32": 208, "3d16": 108}
 FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes per step-kernel launch from an ncu capture (dram__bytes_read.sum
 # + dram__bytes_write.sum) of the workload below, valid only for the kernel
@@ -41,9 +41,10 @@ def kernel_hash(params):
 
 
 def lattice_kind(p):
+    h = p.get("precision", 0) == 1
     if p.get("dim", 2) != 3:
-        return "2d"
-    return "3d16" if p.get("precision", 0) == 1 else "3d32"
+        return "2d16" if h else "2d"
+    return "3d16" if h else "3d32"
 
 
 def cells_of(p):
@@ -56,6 +57,8 @@ def device_bytes(p):
     k = lattice_kind(p)
     if k == "2d":
         return c * 14 * 4 * 2
+    if k == "2d16":
+        return c * 30 * 2
     es = 2 if k == "3d16" else 4
     planes = c // p["nz"] * (p["nz"] + 2)
     return c * (25 * es + 8) + planes * (25 * es + 4)
@@ -63,9 +66,12 @@ def device_bytes(p):
 
 def workload(name, rank=0):
     from paper_1702_04487_gb300 import workloads as W
-    if name == "cfg2":
+    if name in ("cfg2", "cfg2h"):
         ps = W.cfg2_sweep(seed=2 + rank)
         desc = "200x1600 nozzle sweep: 5 contact angles x 4 surface tensions, 20 lattices, FP32"
+        if name == "cfg2h":
+            ps = [dict(p, precision=1) for p in ps]
+            desc = desc.replace("FP32", "FP16 offset storage")
     elif name == "big":
         ps = [W.big_nozzle()]
         desc = "2048x8192 nozzle (200x1600 geometry scaled), 1 lattice, FP32"
@@ -312,7 +318,7 @@ def run_native(args):
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if kind != "3d16" else "f32 (f16 storage)",
+            "dtype": "f32" if kind in ("2d", "3d32") else "f32 (f16 storage)",
             "data": "synthetic",
             "config": {"workload": desc, "lattices": len(params), "cells_per_step": cells,
                        "parallelism": "replicas" if world > 1 else "single",
@@ -324,7 +330,7 @@ def run_native(args):
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind
                          if peak_kind == "measured" else "fallback 6.8 TB/s",
-                         "kernel": "step_kernel" if kind == "2d" else "collide3 + stream3",
+                         "kernel": "step_kernel" if kind in ("2d", "2d16") else "collide3 + stream3",
                          "timed_steps": k_steps, "timed_launches": k_launches,
                          "ms_per_step": per_step_ms, "bytes_per_lup": bpl,
                          "algorithmic_bytes_per_step": bpl * cells},
@@ -371,6 +377,13 @@ def run_surrogate(args):
     t0 = time.perf_counter()
     y_ev = S.lbm_outcomes(x_ev, steps=steps)  # batched: every query a lattice of one handle
     t_batched = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    y_ev16 = S.lbm_outcomes(x_ev, steps=steps, precision=1)  # batched, FP16 storage
+    t_batched16 = time.perf_counter() - t0
+    both = S.finite_rows(y_ev) & S.finite_rows(y_ev16)
+    e16_tb = S.relative_error(y_ev16[both, 0], y_ev[both, 0])
+    e16_v = S.relative_error(y_ev16[both, 1], y_ev[both, 1])
     one = min(8, len(x_ev))
     t0 = time.perf_counter()
     for k in range(one):
@@ -425,6 +438,14 @@ def run_surrogate(args):
                    "train_steps": args.sg_train_steps, "tau": args.sg_tau},
         "lbm_single_runs_per_s": 1.0 / t_single,
         "lbm_batched_runs_per_s": n / t_batched,
+        "lbm_batched_fp16_runs_per_s": n / t_batched16,
+        "fp16_vs_fp32_lbm": {
+            "runs_both_ejecting": int(both.sum()),
+            "ejecting_disagree": int((S.finite_rows(y_ev) != S.finite_rows(y_ev16)).sum()),
+            "breakup_within_1pct": float((e16_tb <= 0.01).mean()) if len(e16_tb) else None,
+            "velocity_within_1pct": float((e16_v <= 0.01).mean()) if len(e16_v) else None,
+            "breakup_p95": float(np.percentile(e16_tb, 95)) if len(e16_tb) else None,
+            "velocity_p95": float(np.percentile(e16_v, 95)) if len(e16_v) else None},
         "surrogate_only_queries_per_s": n / t_pred,
         "accepted": int(acc.sum()), "accepted_ejecting": int(sel.sum()),
         "accepted_not_ejecting": int((acc & ~fin).sum()),
@@ -446,7 +467,8 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=("native", "reference"), default="native")
-    ap.add_argument("--workload", choices=("cfg2", "big", "cfg3", "cfg4", "cfg4h"), default="cfg2")
+    ap.add_argument("--workload", choices=("cfg2", "cfg2h", "big", "cfg3", "cfg4", "cfg4h"),
+                    default="cfg2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the default launch shape instead of timing candidates first")

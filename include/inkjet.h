@@ -80,8 +80,9 @@ typedef enum {
 
 /* population storage */
 #define IJ_FP32 0        /* f as FP32 deviations f_i - w_i n0, g as FP32 */
-#define IJ_FP16_STORE 1  /* 3-D only: f deviations and g_1.. in FP16, g_0 in FP32;
-                            every update is computed in FP32 */
+#define IJ_FP16_STORE 1  /* f deviations and g_1.. in FP16, g_0 in FP32; every
+                            update is computed in FP32.  2-D: nx must be even, and
+                            all lattices of one handle share the precision */
 
 typedef struct {
   int nx, ny;                 /* lattice size, nx, ny >= 1 */
@@ -236,7 +237,8 @@ ij_status ij_get_tuning(ij_handle h, int bucket, int* block_size, int* chunk, in
  * cudaMalloc is not allowed.  It computes exactly what ij_step computes for a
  * one-lattice handle.
  *   params        : the lattice (host memory); nx, ny, geometry as in ij_create;
- *                   2-D only (dim 3 returns IJ_ERR_PARAM).
+ *                   2-D FP32 storage only (dim 3 or IJ_FP16_STORE returns
+ *                   IJ_ERR_PARAM).
  *   t             : time of the input state (selects the drive F(t)).
  *   f_in, g_in    : device, the state at t.  f holds the stored layout
  *                   f_i - w_i n0 on fluid cells (n0 = (rho_ink + rho_air)/2,

@@ -70,10 +70,11 @@ struct ij_handle_s {
   // diagnostics descriptor over its z planes (ny = nz) for the shared
   // record kernel and the observation calls
   bool is3d = false;
+  bool fp16 = false;  // 2-D lattices in FP16 storage
   std::vector<Inst3> inst3;
   Inst3* d_inst3 = nullptr;
-  float* stage3 = nullptr;  // FP32 staging of exported / imported 3-D states
-  size_t stage3_floats = 0;
+  float* stage = nullptr;  // FP32 staging of exported / imported states (3-D, 2-D FP16)
+  size_t stage_floats = 0;
   std::vector<ij_params> params;
   std::vector<Inst> inst;
   std::vector<Item> items;
@@ -170,8 +171,10 @@ ij_status validate(const ij_params& p, int k) {
   if (p.init_kind < 0 || p.init_kind > 3) return fail(IJ_ERR_PARAM, "lattice %d: bad init_kind", k);
   const int dim = p.dim == 0 ? 2 : p.dim;
   if (dim != 2 && dim != 3) return fail(IJ_ERR_PARAM, "lattice %d: dim must be 2 or 3", k);
-  if (p.precision != IJ_FP32 && !(dim == 3 && p.precision == IJ_FP16_STORE))
-    return fail(IJ_ERR_PARAM, "lattice %d: unsupported precision (FP16 storage is 3-D only)", k);
+  if (p.precision != IJ_FP32 && p.precision != IJ_FP16_STORE)
+    return fail(IJ_ERR_PARAM, "lattice %d: precision must be IJ_FP32 or IJ_FP16_STORE", k);
+  if (dim == 2 && p.precision == IJ_FP16_STORE && p.nx % 2 != 0)
+    return fail(IJ_ERR_PARAM, "lattice %d: 2-D FP16 storage needs an even nx", k);
   if (dim == 3) {
     if (p.nz < 1) return fail(IJ_ERR_PARAM, "lattice %d: nz must be >= 1", k);
     if (p.nz > 65533 || p.ny > 262140)  // grid limits of the 32 x 4 x 1 blocks
@@ -210,6 +213,7 @@ Inst derive(const ij_params& p) {
   I.wt = p.wall_thickness;
   I.bc = p.axial_bc;
   I.init_kind = p.init_kind;
+  I.fp16 = (p.dim == 0 || p.dim == 2) && p.precision == IJ_FP16_STORE;
   const double phis = 0.5 * (p.rho_ink - p.rho_air), n0 = 0.5 * (p.rho_ink + p.rho_air);
   const double A = 3.0 * p.sigma / (8.0 * p.width_W * phis * phis * phis * phis);
   const double kappa = 3.0 * p.sigma * p.width_W / (4.0 * phis * phis);
@@ -422,7 +426,7 @@ ij_status one_step(ij_handle h) {
       CUDA_TRY(cudaEventRecord(e0, h->stream));
     }
     CUDA_TRY(launch_step(h->d_inst, h->d_items + b.first, b.count, b.nthreads, b.grid, h->d_t, 0,
-                         diag, b.prefetch, h->stream));
+                         diag, b.prefetch, h->fp16, h->stream));
     h->launches++;
     if (h->timing) {
       CUDA_TRY(cudaEventRecord(e1, h->stream));
@@ -459,7 +463,7 @@ ij_status build_graph(ij_handle h) {
     }
     for (const Bucket& b : h->buckets) {
       e = launch_step(h->d_inst, h->d_items + b.first, b.count, b.nthreads, b.grid, h->d_t, j,
-                      diag, b.prefetch, cs);
+                      diag, b.prefetch, h->fp16, cs);
       n++;
       if (e != cudaSuccess) break;
     }
@@ -554,12 +558,12 @@ ij_status create3(ij_handle h) {
   return IJ_OK;
 }
 
-// FP32 staging buffer for exporting / importing a 3-D lattice's state.
-ij_status ensure_stage3(ij_handle h, size_t floats) {
-  if (h->stage3_floats >= floats) return IJ_OK;
-  h->stage3 = (float*)h->dalloc(floats * sizeof(float));
-  if (!h->stage3) return fail(IJ_ERR_OOM, "device allocation of the 3-D staging buffer failed");
-  h->stage3_floats = floats;
+// FP32 staging buffer for exporting / importing a lattice's state (3-D, 2-D FP16).
+ij_status ensure_stage(ij_handle h, size_t floats) {
+  if (h->stage_floats >= floats) return IJ_OK;
+  h->stage = (float*)h->dalloc(floats * sizeof(float));
+  if (!h->stage) return fail(IJ_ERR_OOM, "device allocation of the staging buffer failed");
+  h->stage_floats = floats;
   return IJ_OK;
 }
 
@@ -567,13 +571,13 @@ ij_status ensure_stage3(ij_handle h, size_t floats) {
 ij_status get_state3(ij_handle h, int index, float* f, float* g, int on_device) {
   const Inst3& J = h->inst3[index];
   const size_t N = (size_t)J.nx * J.ny * J.nz;
-  ij_status st = ensure_stage3(h, 26 * N);
+  ij_status st = ensure_stage(h, 26 * N);
   if (st != IJ_OK) return st;
-  CUDA_TRY(launch_export3(h->d_inst3, J, index, h->stage3, h->stage3 + 19 * N, h->stream));
+  CUDA_TRY(launch_export3(h->d_inst3, J, index, h->stage, h->stage + 19 * N, h->stream));
   h->launches++;
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-  if (f) CUDA_TRY(cudaMemcpyAsync(f, h->stage3, 19 * N * sizeof(float), kind, h->stream));
-  if (g) CUDA_TRY(cudaMemcpyAsync(g, h->stage3 + 19 * N, 7 * N * sizeof(float), kind, h->stream));
+  if (f) CUDA_TRY(cudaMemcpyAsync(f, h->stage, 19 * N * sizeof(float), kind, h->stream));
+  if (g) CUDA_TRY(cudaMemcpyAsync(g, h->stage + 19 * N, 7 * N * sizeof(float), kind, h->stream));
   CUDA_TRY(cudaStreamSynchronize(h->stream));
   return IJ_OK;
 }
@@ -584,12 +588,12 @@ ij_status set_state3(ij_handle h, int index, const float* f, const float* g, lon
                      int on_device) {
   const Inst3& J = h->inst3[index];
   const size_t N = (size_t)J.nx * J.ny * J.nz;
-  ij_status st = ensure_stage3(h, 26 * N);
+  ij_status st = ensure_stage(h, 26 * N);
   if (st != IJ_OK) return st;
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  CUDA_TRY(cudaMemcpyAsync(h->stage3, f, 19 * N * sizeof(float), kind, h->stream));
-  CUDA_TRY(cudaMemcpyAsync(h->stage3 + 19 * N, g, 7 * N * sizeof(float), kind, h->stream));
-  CUDA_TRY(launch_import3(h->d_inst3, J, index, h->stage3, h->stage3 + 19 * N, h->stream));
+  CUDA_TRY(cudaMemcpyAsync(h->stage, f, 19 * N * sizeof(float), kind, h->stream));
+  CUDA_TRY(cudaMemcpyAsync(h->stage + 19 * N, g, 7 * N * sizeof(float), kind, h->stream));
+  CUDA_TRY(launch_import3(h->d_inst3, J, index, h->stage, h->stage + 19 * N, h->stream));
   h->launches++;
   CUDA_TRY(cudaMemcpyAsync(h->d_t, &t, sizeof(long long), cudaMemcpyHostToDevice, h->stream));
   const double dinit[8] = {0, 0, 0, -1, 0, 0, 0, 0};
@@ -598,6 +602,39 @@ ij_status set_state3(ij_handle h, int index, const float* f, const float* g, lon
   CUDA_TRY(cudaStreamSynchronize(h->stream));
   h->t = t;
   h->drop_graph();
+  return IJ_OK;
+}
+
+// Absolute FP32 populations of a 2-D lattice in FP16 storage, decoded
+// through the staging buffer (the other time buffer is too small for FP32).
+ij_status get_state16(ij_handle h, int index, float* f, float* g, int on_device) {
+  const Inst& I = h->inst[index];
+  const size_t N = (size_t)I.nx * I.ny;
+  ij_status st = ensure_stage(h, 14 * N);
+  if (st != IJ_OK) return st;
+  CUDA_TRY(launch_convert16(h->d_inst, I, index, (int)(h->t & 1), h->stage, h->stage + 9 * N,
+                            false, h->stream));
+  h->launches++;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (f) CUDA_TRY(cudaMemcpyAsync(f, h->stage, 9 * N * sizeof(float), kind, h->stream));
+  if (g) CUDA_TRY(cudaMemcpyAsync(g, h->stage + 9 * N, 5 * N * sizeof(float), kind, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return IJ_OK;
+}
+
+// Encode absolute FP32 populations into the FP16 state of time parity t.
+ij_status set_state16(ij_handle h, int index, const float* f, const float* g, long long t,
+                      int on_device) {
+  const Inst& I = h->inst[index];
+  const size_t N = (size_t)I.nx * I.ny;
+  ij_status st = ensure_stage(h, 14 * N);
+  if (st != IJ_OK) return st;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CUDA_TRY(cudaMemcpyAsync(h->stage, f, 9 * N * sizeof(float), kind, h->stream));
+  CUDA_TRY(cudaMemcpyAsync(h->stage + 9 * N, g, 5 * N * sizeof(float), kind, h->stream));
+  CUDA_TRY(launch_convert16(h->d_inst, I, index, (int)(t & 1), h->stage, h->stage + 9 * N, true,
+                            h->stream));
+  h->launches++;
   return IJ_OK;
 }
 
@@ -654,13 +691,17 @@ ij_status ij_create(const ij_params* params, int count, ij_alloc_fn alloc, ij_fr
     *out = h;
     return IJ_OK;
   }
+  // one step launch covers every lattice, so they share one storage format
+  for (int k = 1; k < count; k++)
+    if (params[k].precision != params[0].precision)
+      return bail(fail(IJ_ERR_PARAM, "all 2-D lattices of a batch must share the precision"));
+  h->fp16 = params[0].precision == IJ_FP16_STORE;
   h->inst.resize(count);
   for (int k = 0; k < count; k++) {
     Inst I = derive(params[k]);
-    const size_t N = (size_t)I.nx * I.ny;
     for (int b = 0; b < 2; b++) {
-      I.f[b] = (float*)h->dalloc(9 * N * sizeof(float));
-      I.g[b] = (float*)h->dalloc(5 * N * sizeof(float));
+      I.f[b] = (float*)h->dalloc(state_bytes_f(I));
+      I.g[b] = (float*)h->dalloc(state_bytes_g(I));
       if (!I.f[b] || !I.g[b]) return bail(fail(IJ_ERR_OOM, "device allocation of lattice %d failed", k));
     }
     I.rows = (double*)h->dalloc(3 * (size_t)I.ny * sizeof(double));
@@ -755,10 +796,10 @@ ij_status ij_observe(ij_handle h, int index, ij_obs* out, float* phi_out, int ph
     const Inst3& J = h->inst3[index];
     const size_t N3 = (size_t)J.nx * J.ny * J.nz;
     if (!phi_on_device) {
-      st = ensure_stage3(h, N3);
+      st = ensure_stage(h, N3);
       if (st != IJ_OK) return st;
     }
-    float* dst = phi_on_device ? phi_out : h->stage3;
+    float* dst = phi_on_device ? phi_out : h->stage;
     CUDA_TRY(launch_phi3(h->d_inst3, J, index, dst, h->stream));
     h->launches++;
     if (!phi_on_device)
@@ -819,6 +860,7 @@ ij_status ij_get_state(ij_handle h, int index, float* f, float* g, int on_device
   if (st != IJ_OK) return st;
   if (index < 0 || index >= h->n_inst) return fail(IJ_ERR_PARAM, "index out of range");
   if (h->is3d) return get_state3(h, index, f, g, on_device);
+  if (h->fp16) return get_state16(h, index, f, g, on_device);
   const Inst& I = h->inst[index];
   const size_t N = (size_t)I.nx * I.ny;
   cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
@@ -852,17 +894,21 @@ ij_status ij_set_state(ij_handle h, int index, const float* f, const float* g, l
     for (int k = 0; k < h->n_inst; k++) {
       if (k == index) continue;
       const Inst& J = h->inst[k];
-      const size_t M = (size_t)J.nx * J.ny;
-      CUDA_TRY(cudaMemcpyAsync(J.f[t & 1], J.f[h->t & 1], 9 * M * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
-      CUDA_TRY(cudaMemcpyAsync(J.g[t & 1], J.g[h->t & 1], 5 * M * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+      CUDA_TRY(cudaMemcpyAsync(J.f[t & 1], J.f[h->t & 1], state_bytes_f(J), cudaMemcpyDeviceToDevice, h->stream));
+      CUDA_TRY(cudaMemcpyAsync(J.g[t & 1], J.g[h->t & 1], state_bytes_g(J), cudaMemcpyDeviceToDevice, h->stream));
     }
   }
   const Inst& I = h->inst[index];
-  const size_t N = (size_t)I.nx * I.ny;
-  CUDA_TRY(cudaMemcpyAsync(I.f[(t + 1) & 1], f, 9 * N * sizeof(float), kind, h->stream));
-  CUDA_TRY(launch_f_import(h->d_inst, I, index, I.f[(t + 1) & 1], I.f[t & 1], h->stream));
-  h->launches++;
-  CUDA_TRY(cudaMemcpyAsync(I.g[t & 1], g, 5 * N * sizeof(float), kind, h->stream));
+  if (h->fp16) {
+    st = set_state16(h, index, f, g, t, on_device);
+    if (st != IJ_OK) return st;
+  } else {
+    const size_t N = (size_t)I.nx * I.ny;
+    CUDA_TRY(cudaMemcpyAsync(I.f[(t + 1) & 1], f, 9 * N * sizeof(float), kind, h->stream));
+    CUDA_TRY(launch_f_import(h->d_inst, I, index, I.f[(t + 1) & 1], I.f[t & 1], h->stream));
+    h->launches++;
+    CUDA_TRY(cudaMemcpyAsync(I.g[t & 1], g, 5 * N * sizeof(float), kind, h->stream));
+  }
   CUDA_TRY(cudaMemcpyAsync(h->d_t, &t, sizeof(long long), cudaMemcpyHostToDevice, h->stream));
   const double dinit[8] = {0, 0, 0, -1, 0, 0, 0, 0};
   for (int k = 0; k < h->n_inst; k++) {
@@ -955,11 +1001,11 @@ ij_status ij_autotune(ij_handle h, int reps) {
         if (st != IJ_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return st; }
         const Bucket& b = h->buckets[bi];
         CUDA_TRY(launch_step(h->d_inst, h->d_items + b.first, b.count, nt, b.grid, h->d_t, 0,
-                             false, pf, h->stream));  // warm-up
+                             false, pf, h->fp16, h->stream));  // warm-up
         CUDA_TRY(cudaEventRecord(e0, h->stream));
         for (int r = 0; r < reps; r++)
           CUDA_TRY(launch_step(h->d_inst, h->d_items + b.first, b.count, nt, b.grid, h->d_t, 0,
-                               false, pf, h->stream));
+                               false, pf, h->fp16, h->stream));
         CUDA_TRY(cudaEventRecord(e1, h->stream));
         CUDA_TRY(cudaEventSynchronize(e1));
         float ms = 0.0f;

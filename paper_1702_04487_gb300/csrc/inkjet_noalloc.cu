@@ -86,6 +86,8 @@ extern "C" ij_status ij_step_noalloc(const ij_params* params, long long t, const
   if (st != IJ_OK) return st;
   const ij_params& p = *params;
   if (p.dim == 3) return report(IJ_ERR_PARAM, "ij_step_noalloc: 2-D lattices only");
+  if (p.precision != IJ_FP32)
+    return report(IJ_ERR_PARAM, "ij_step_noalloc: FP32 storage only");
   if (p.ny > kMaxRows)
     return report(IJ_ERR_PARAM, "ij_step_noalloc: ny exceeds the fixed scratch limit of 8192 rows");
   // work list: the same strips and row chunks ij_create builds for one lattice
@@ -131,7 +133,7 @@ extern "C" ij_status ij_step_noalloc(const ij_params* params, long long t, const
   }
   NOALLOC_TRY(launch_step(d_inst, d_items, n_items, kStepThreads,
                           (n_items + kStepThreads / 32 - 1) / (kStepThreads / 32), d_t, 0, diag,
-                          step_prefetch_for(kStepThreads), s));
+                          step_prefetch_for(kStepThreads), false, s));
   if (diag) {
     NOALLOC_TRY(launch_finalize(d_inst, 1, d_t, s));
     NOALLOC_TRY(cudaMemcpyAsync(record_out, base + kOffHist, kRec * sizeof(double),

@@ -20,7 +20,8 @@ constexpr unsigned kStatusNumeric = 1u;
 // initialisation and the diagnostics.
 struct Inst {
   int nx, ny, geom, cx0, cx1, L, wt, bc;
-  int y_exit, y_scan, init_kind, pad0;
+  int y_exit, y_scan, init_kind;
+  int fp16;  // FP16 storage (the same for every lattice of a handle)
   // step constants (FP32)
   float phis, inv_phis, A4, kappa, hk, q, omq, inv_tphi, gamma, inv2q, nu_air, dnu, F0, Fneg;
   float n0;  // rest density: f is stored as the deviation f_i - w_i n0
@@ -31,7 +32,9 @@ struct Inst {
   // populations, double-buffered by time parity: f[t & 1] holds the state at
   // t.  f holds deviations from the rest equilibrium, f_i - w_i n0, so that
   // FP32 rounds the small part that varies (about 50x smaller ulp); g is
-  // stored as is.
+  // stored as is.  FP16 storage: f as 9N halves; g as g_0 in FP32 [N]
+  // followed by g_1..4 as halves [4][N] (nx even, so pairs of halves of
+  // neighbouring columns are 4-byte aligned).
   float* f[2];
   float* g[2];
   // diagnostics scratch and results
@@ -53,7 +56,10 @@ constexpr int kStepThreads = 32;  // one warp per block, one work item each
 constexpr int kStepBlocksPerSM = 16;  // resident blocks per SM (registers: 128 each)
 constexpr int kMaxPrefetch = 4;    // rows staged ahead of use: 1 .. 4
 
-size_t step_smem_bytes(int nthreads, int prefetch);
+size_t step_smem_bytes(int nthreads, int prefetch, bool h16);
+// bytes of one time buffer of f / of g
+size_t state_bytes_f(const Inst& I);
+size_t state_bytes_g(const Inst& I);
 cudaError_t set_step_smem_limit();
 // Work items of one lattice (row chunks of `chunk` rows x strips) into out
 // (at most cap); returns the count, or -1 when cap is too small.
@@ -71,7 +77,7 @@ ij_status report(ij_status st, const char* msg);
 cudaError_t launch_init(const Inst* d_inst, const Inst& h_inst, int index, cudaStream_t s);
 cudaError_t launch_step(const Inst* d_inst, const Item* d_items, int n_items, int nthreads,
                         int grid, const long long* d_t, int t_off, bool diag, int prefetch,
-                        cudaStream_t s);
+                        bool h16, cudaStream_t s);
 // default number of rows staged ahead of use
 int step_prefetch_for(int nthreads);
 cudaError_t launch_finalize(const Inst* d_inst, int n_inst, const long long* d_t,
@@ -84,5 +90,9 @@ cudaError_t launch_f_export(const Inst* d_inst, const Inst& h_inst, int index, c
                             float* dst, cudaStream_t s);
 cudaError_t launch_f_import(const Inst* d_inst, const Inst& h_inst, int index, const float* src,
                             float* dst, cudaStream_t s);
+// FP16 storage of time parity `parity` <-> absolute FP32 f [9][N], g [5][N]
+// (export when !to_device_state; f or g may be null on export)
+cudaError_t launch_convert16(const Inst* d_inst, const Inst& h_inst, int index, int parity,
+                             float* f, float* g, bool to_device_state, cudaStream_t s);
 
 }  // namespace ij

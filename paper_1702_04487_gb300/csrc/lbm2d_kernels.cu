@@ -2,18 +2,22 @@
 // (He et al., arXiv:1702.04487, "Methods", Eq. 3-10).
 //
 // Step kernel design (bandwidth-bound stencil, no tensor cores):
-//  - one thread per lattice column; a block owns a strip of columns and a
-//    chunk of rows and marches up the rows, so every cell's populations are
-//    read once and written once per step (structure-of-arrays, coalesced);
-//  - per row iteration, four pipelined stages over shared-memory ring
-//    buffers of three rows: (1) phi = sum g of row R, (2) wetting ghost
-//    values of row R-1, (3) chemical potential, forces, velocity and the
-//    collision of f (Eq. 4-6) and g (Eq. 8-10) on row R-2, (4) streaming of
+//  - one warp per work item: a strip of 28 written columns (plus two halo
+//    columns each side) by a chunk of rows of one lattice; the warp marches
+//    up the rows, so every cell's populations are read once and written
+//    once per step (structure-of-arrays, coalesced);
+//  - neighbours along x come from warp shuffles, along y from registers;
+//    populations are staged P rows ahead with cp.async into a per-warp ring
+//    in shared memory, and warps never wait on one another;
+//  - per row iteration: phi of row R, wetting ghost values of row R-1, the
+//    collision of f (Eq. 4-6) and g (Eq. 8-10) on row R-2, the streaming of
 //    row R-3 with halfway bounce-back and the stay/move split of Eq. 8;
-//  - geometry is analytic (no mask array) and the x-halo of a strip is
-//    recomputed by its two edge threads;
-//  - diagnostics rows (ink weight, mass, momentum) are reduced in FP64 by
-//    warp shuffles and atomics inside the same pass on diagnostics steps.
+//  - geometry is analytic (no mask array);
+//  - storage is FP32, or FP16 (f as offsets from w_i n0, g_1..4 as is, g_0
+//    in FP32) with every update in FP32;
+//  - diagnostics rows (ink weight, mass, momentum) are summed in FP32 per
+//    strip row and in FP64 across rows and strips, on diagnostics steps.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -140,6 +144,40 @@ __device__ __forceinline__ void cp4_if(unsigned sa, const float* p, int N, bool 
       "l"(p), "l"(p + N), "l"(p + 2 * N), "l"(p + 3 * N), "r"((int)pred)
       : "memory");
 }
+// FP16 storage: one 4-byte copy, and groups of 4 / 5 copies of the 4-byte
+// half pairs at p, p + N, ... (halves) into sa, sa + DS, ...
+__device__ __forceinline__ void cp1_if(unsigned sa, const void* p, bool pred) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %2, 0;\n"
+      " @p cp.async.ca.shared.global [%0], [%1], 4;\n}\n" ::"r"(sa),
+      "l"(p), "r"((int)pred)
+      : "memory");
+}
+template <int DS>
+__device__ __forceinline__ void cp4h_if(unsigned sa, const __half* p, int N, bool pred) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %5, 0;\n"
+      " @p cp.async.ca.shared.global [%0], [%1], 4;\n"
+      " @p cp.async.ca.shared.global [%0+%6], [%2], 4;\n"
+      " @p cp.async.ca.shared.global [%0+%7], [%3], 4;\n"
+      " @p cp.async.ca.shared.global [%0+%8], [%4], 4;\n}\n" ::"r"(sa),
+      "l"(p), "l"(p + N), "l"(p + 2 * N), "l"(p + 3 * N), "r"((int)pred), "n"(DS), "n"(2 * DS),
+      "n"(3 * DS)
+      : "memory");
+}
+template <int DS>
+__device__ __forceinline__ void cp5h_if(unsigned sa, const __half* p, int N, bool pred) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %6, 0;\n"
+      " @p cp.async.ca.shared.global [%0], [%1], 4;\n"
+      " @p cp.async.ca.shared.global [%0+%7], [%2], 4;\n"
+      " @p cp.async.ca.shared.global [%0+%8], [%3], 4;\n"
+      " @p cp.async.ca.shared.global [%0+%9], [%4], 4;\n"
+      " @p cp.async.ca.shared.global [%0+%10], [%5], 4;\n}\n" ::"r"(sa),
+      "l"(p), "l"(p + N), "l"(p + 2 * N), "l"(p + 3 * N), "l"(p + 4 * N), "r"((int)pred),
+      "n"(DS), "n"(2 * DS), "n"(3 * DS), "n"(4 * DS)
+      : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() {
   asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
@@ -192,20 +230,53 @@ __device__ __forceinline__ int column_kind(const Inst& I, int x) {
 // to the other time buffer.  Every lane stages its own column's 14
 // populations of row R+P into the warp's shared-memory ring with cp.async,
 // P rows ahead of use, and reads back only what it staged itself.
+//
+// FP16 storage (H): a cp.async moves 4 bytes at least, so each even lane
+// stages the half pair of its own column and the next (x even: strips start
+// at even columns and nx is even, so a pair never straddles the wrap); every
+// lane stages its FP32 g_0; the edge lanes stage the outer column's g into
+// slots of their own.  One staged row holds (in 4-byte words) g_0[32],
+// g_1..4 as [4][16] half pairs, f_0..8 as [9][16] half pairs, then the outer
+// g_0 and g_1..4 pairs of lane 0 and of lane 31.
 constexpr int kWarpsPerBlock = kStepThreads / 32;
 constexpr int kRowFloats = 14 * 32;  // one staged row of a warp: g[5][32], then f[9][32]
+constexpr int kRowWordsH = 256;      // the same in FP16 storage (250 used)
 constexpr unsigned kFull = 0xffffffffu;
 
-template <bool DIAG, int P>
+template <bool DIAG, int P, bool H>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, kStepBlocksPerSM)
     step_kernel(const Inst* __restrict__ insts, const Item* __restrict__ items, int n_items,
                 const long long* __restrict__ d_t, int t_off) {
   constexpr int D = P + 3;  // ring rows: R+P .. R-2 are live
+  constexpr int kRowW = H ? kRowWordsH : kRowFloats;
   extern __shared__ float4 smem4[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float* ring = reinterpret_cast<float*>(smem4) + warp * D * kRowFloats + lane;
+  // FP32: each lane's column of the ring; FP16: the warp's ring
+  float* ring = reinterpret_cast<float*>(smem4) + warp * D * kRowW + (H ? 0 : lane);
   const unsigned ring_sa = (unsigned)__cvta_generic_to_shared(ring);
   const long long t = *d_t + t_off;
+  // staged g_i / f_i of this lane's column, and the sum of the outer g
+  auto ring_g = [&](const float* row, int i) -> float {
+    if (!H) return row[i * 32];
+    if (i == 0) return row[lane];
+    return __half2float(reinterpret_cast<const __half*>(row + 32 + (i - 1) * 16)[lane]);
+  };
+  auto ring_f = [&](const float* row, int i) -> float {
+    if (!H) return row[(5 + i) * 32];
+    return __half2float(reinterpret_cast<const __half*>(row + 96 + i * 16)[lane]);
+  };
+  auto ring_outer = [&](const float* row) -> float {
+    if (!H) return row[160] + row[192] + row[224] + row[256] + row[288];
+    // lane 0: outer column x - 1 is odd, the upper half; lane 31: x + 1 even
+    const float* o = row + 240 + (lane == 0 ? 0 : 5);
+    float sum = o[0];
+#pragma unroll
+    for (int i = 1; i < 5; i++) {
+      const __half2 hp = reinterpret_cast<const __half2*>(o)[i];
+      sum += lane == 0 ? __high2float(hp) : __low2float(hp);
+    }
+    return sum;
+  };
 
   for (int item = blockIdx.x * kWarpsPerBlock + warp; item < n_items;
        item += gridDim.x * kWarpsPerBlock) {
@@ -237,23 +308,48 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kStepBlocksPerSM)
     const float* __restrict__ gin = I.g[t & 1];
     float* __restrict__ fout = I.f[(t + 1) & 1];
     float* __restrict__ gout = I.g[(t + 1) & 1];
+    // FP16 storage: f halves; g_0 FP32 [N], then g_1..4 halves [4][N]
+    const __half* __restrict__ fhin = reinterpret_cast<const __half*>(fin);
+    const __half* __restrict__ ghin = reinterpret_cast<const __half*>(gin + N);
+    __half* __restrict__ fhout = reinterpret_cast<__half*>(fout);
+    __half* __restrict__ ghout = reinterpret_cast<__half*>(gout + N);
+    const bool any_edge = H && __any_sync(kFull, edge);
 
     // Stage pipeline row r into ring slot sp (own column; f only for rows
     // that are collided), as one cp.async group.
     auto stage = [&](int r, int sp) {
       int ym;
       if (r <= y0 + ch + 2 && map_row_v(r, ny, bc, ym)) {  // uniform over the warp
-        const unsigned d = ring_sa + sp * (kRowFloats * 4);
+        const unsigned d = ring_sa + sp * (kRowW * 4);
         const bool own = row_kind(geom, ck, L, wt, ym) == 0;
-        const bool fneed = own && col_lane && r >= y0 - 1 && r <= y0 + ch;
+        const bool frow = r >= y0 - 1 && r <= y0 + ch;
         // a solid edge lane has no populations of its own: the g of the
         // column outside the strip go where its f would be
         const bool outer = edge && !own && row_kind(geom, cko, L, wt, ym) == 0;
-        const float* qg = gin + (ym * nx + x);
-        const float* qf = outer ? gin + (ym * nx + xo) : fin + (ym * nx + x);
-        cp5_if(d, qg, N, own);
-        cp5_if(d + 5 * 128, qf, N, fneed || outer);
-        cp4_if(d + 10 * 128, qf + 5 * N, N, fneed);
+        if (!H) {
+          const bool fneed = own && col_lane && frow;
+          const float* qg = gin + (ym * nx + x);
+          const float* qf = outer ? gin + (ym * nx + xo) : fin + (ym * nx + x);
+          cp5_if(d, qg, N, own);
+          cp5_if(d + 5 * 128, qf, N, fneed || outer);
+          cp4_if(d + 10 * 128, qf + 5 * N, N, fneed);
+        } else {
+          const int c = ym * nx + x;
+          cp1_if(d + lane * 4, gin + c, own);
+          // the even lane of a pair copies for both (x + 1 has kind ckE)
+          const bool pair = (lane & 1) == 0 && (own || row_kind(geom, ckE, L, wt, ym) == 0);
+          const bool fpair = pair && frow && lane <= it.halo + it.nout;
+          const unsigned dp = d + (lane >> 1) * 4;
+          cp4h_if<64>(dp + 128, ghin + c, N, pair);
+          cp5h_if<64>(dp + 384, fhin + c, N, fpair);
+          cp4h_if<64>(dp + 384 + 5 * 64, fhin + 5 * N + c, N, fpair);
+          if (any_edge) {
+            const int co = ym * nx + xo;
+            const unsigned dq = d + 960 + (lane == 0 ? 0 : 20);
+            cp1_if(dq, gin + co, outer);
+            cp4h_if<4>(dq + 4, ghin + (co & ~1), N, outer);
+          }
+        }
       }
       cp_async_commit();
     };
@@ -312,10 +408,12 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kStepBlocksPerSM)
         int ym;
         m0 = map_row_v(R, ny, bc, ym) ? ym : -1;
         k0 = m0 >= 0 ? row_kind(geom, ck, L, wt, m0) : 1;
-        const float* sg = ring + sl * kRowFloats;
-        pr0 = k0 == 0 ? sg[0] + sg[32] + sg[64] + sg[96] + sg[128] : 0.0f;
+        const float* sg = ring + sl * kRowW;
+        pr0 = k0 == 0 ? ring_g(sg, 0) + ring_g(sg, 1) + ring_g(sg, 2) + ring_g(sg, 3) +
+                            ring_g(sg, 4)
+                      : 0.0f;
         px0 = edge && k0 != 0 && m0 >= 0 && row_kind(geom, cko, L, wt, m0) == 0
-                  ? sg[160] + sg[192] + sg[224] + sg[256] + sg[288]
+                  ? ring_outer(sg)
                   : 0.0f;
       }
       // ---- phi with wetting ghosts of row R-1
@@ -370,12 +468,12 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kStepBlocksPerSM)
         if (k >= 4 && col_lane && k2 == 0) {
           int s2 = sl - 2;
           if (s2 < 0) s2 += D;
-          const float* sg = ring + s2 * kRowFloats;
+          const float* sg = ring + s2 * kRowW;
           float g2[5], fr[9];
 #pragma unroll
-          for (int i = 0; i < 5; i++) g2[i] = sg[i * 32];
+          for (int i = 0; i < 5; i++) g2[i] = ring_g(sg, i);
 #pragma unroll
-          for (int i = 0; i < 9; i++) fr[i] = sg[(5 + i) * 32];
+          for (int i = 0; i < 9; i++) fr[i] = ring_f(sg, i);
           const float pC = pe1;
           // lap = 6 sum_i w_i (phi_i - phi) from the differences, which are
           // exact where neighbours are close (no cancellation of O(10) terms)
@@ -519,15 +617,28 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kStepBlocksPerSM)
               if (sm & (1u << 8)) fn[8] = cB[5];
             }
           }
-          float* fo = fout + Y * nx + x;
-          float* go = gout + Y * nx + x;
+          if (!H) {
+            float* fo = fout + Y * nx + x;
+            float* go = gout + Y * nx + x;
 #pragma unroll
-          for (int i = 0; i < 9; i++) fo[i * N] = fn[i];
-          go[0] = oB[1];
-          go[N] = oB[2] + P1;
-          go[2 * N] = oB[3] + P2;
-          go[3 * N] = oB[4] + P3;
-          go[4 * N] = oB[5] + P4;
+            for (int i = 0; i < 9; i++) fo[i * N] = fn[i];
+            go[0] = oB[1];
+            go[N] = oB[2] + P1;
+            go[2 * N] = oB[3] + P2;
+            go[3 * N] = oB[4] + P3;
+            go[4 * N] = oB[5] + P4;
+          } else {
+            // round to nearest even on store
+            __half* fo = fhout + Y * nx + x;
+            __half* go = ghout + Y * nx + x;
+#pragma unroll
+            for (int i = 0; i < 9; i++) fo[i * N] = __float2half_rn(fn[i]);
+            gout[Y * nx + x] = oB[1];
+            go[0] = __float2half_rn(oB[2] + P1);
+            go[N] = __float2half_rn(oB[3] + P2);
+            go[2 * N] = __float2half_rn(oB[4] + P3);
+            go[3 * N] = __float2half_rn(oB[5] + P4);
+          }
         }
       }
       cA[0] = cB[1];  // f*_2
@@ -634,9 +745,24 @@ __global__ void init_pop_kernel(const Inst* __restrict__ insts, int index, const
   const size_t N = (size_t)I.nx * I.ny, cc = (size_t)y * I.nx + x;
   float* f = I.f[0];  // deviations f_i - w_i n0
   float* g = I.g[0];
+  // FP16 storage: f halves, g_0 FP32, g_1..4 halves after it
+  __half* fh = reinterpret_cast<__half*>(f);
+  __half* gh = reinterpret_cast<__half*>(g + N);
+  auto put_f = [&](int i, float v) {
+    if (I.fp16)
+      fh[i * N + cc] = __float2half_rn(v);
+    else
+      f[i * N + cc] = v;
+  };
+  auto put_g = [&](int i, float v) {
+    if (I.fp16 && i > 0)
+      gh[(i - 1) * N + cc] = __float2half_rn(v);
+    else
+      g[i * N + cc] = v;
+  };
   if (geom_kind(I, x, y) != 0) {
-    for (int i = 0; i < 9; i++) f[i * N + cc] = 0.0f;
-    for (int i = 0; i < 5; i++) g[i * N + cc] = 0.0f;
+    for (int i = 0; i < 9; i++) put_f(i, 0.0f);
+    for (int i = 0; i < 5; i++) put_g(i, 0.0f);
     return;
   }
   const double wt[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
@@ -649,10 +775,10 @@ __global__ void init_pop_kernel(const Inst* __restrict__ insts, int index, const
   const double n = I.d_n0, p = p0 * mu + n / 3.0;
   for (int i = 0; i < 9; i++) {
     double Ai = i == 0 ? 2.25 * n - 3.75 * p : 3.0 * p;
-    f[i * N + cc] = (float)(wt[i] * Ai - wt[i] * n);
+    put_f(i, (float)(wt[i] * Ai - wt[i] * n));
   }
-  g[cc] = (float)(p0 - 2.0 * I.d_gamma * mu);
-  for (int i = 1; i < 5; i++) g[i * N + cc] = (float)(0.5 * I.d_gamma * mu);
+  put_g(0, (float)(p0 - 2.0 * I.d_gamma * mu));
+  for (int i = 1; i < 5; i++) put_g(i, (float)(0.5 * I.d_gamma * mu));
 }
 
 __global__ void zero_kernel(float* a, size_t n) {
@@ -796,9 +922,47 @@ __global__ void phi_kernel(const Inst* __restrict__ insts, int index, const long
   const size_t N = (size_t)I.nx * I.ny, cc = (size_t)y * I.nx + x;
   const float* g = I.g[*d_t & 1];
   float p = 0.0f;
-  if (geom_kind(I, x, y) == 0)
-    for (int i = 0; i < 5; i++) p += g[i * N + cc];
+  if (geom_kind(I, x, y) == 0) {
+    if (I.fp16) {
+      const __half* gh = reinterpret_cast<const __half*>(g + N);
+      p = g[cc];
+      for (int i = 0; i < 4; i++) p += __half2float(gh[i * N + cc]);
+    } else {
+      for (int i = 0; i < 5; i++) p += g[i * N + cc];
+    }
+  }
   out[cc] = p;
+}
+
+// FP16 storage <-> absolute FP32 populations f [9][N], g [5][N] of the
+// state at time parity `par` (solid cells 0); rounding to nearest on import.
+template <bool EXPORT>
+__global__ void convert16_kernel(const Inst* __restrict__ insts, int index, int par, float* f,
+                                 float* g) {
+  const Inst& I = insts[index];
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  if (x >= I.nx) return;
+  const size_t N = (size_t)I.nx * I.ny, cc = (size_t)y * I.nx + x;
+  const bool fluid = geom_kind(I, x, y) == 0;
+  __half* fh = reinterpret_cast<__half*>(I.f[par]);
+  float* g0 = I.g[par];
+  __half* gh = reinterpret_cast<__half*>(g0 + N);
+  const float wt[9] = {4.0f / 9, 1.0f / 9, 1.0f / 9, 1.0f / 9, 1.0f / 9,
+                       1.0f / 36, 1.0f / 36, 1.0f / 36, 1.0f / 36};
+  if (EXPORT) {
+    if (f)
+      for (int i = 0; i < 9; i++)
+        f[i * N + cc] = fluid ? __half2float(fh[i * N + cc]) + wt[i] * I.n0 : 0.0f;
+    if (g) {
+      g[cc] = fluid ? g0[cc] : 0.0f;
+      for (int i = 1; i < 5; i++) g[i * N + cc] = fluid ? __half2float(gh[(i - 1) * N + cc]) : 0.0f;
+    }
+  } else {
+    for (int i = 0; i < 9; i++)
+      fh[i * N + cc] = __float2half_rn(fluid ? f[i * N + cc] - wt[i] * I.n0 : 0.0f);
+    g0[cc] = fluid ? g[cc] : 0.0f;
+    for (int i = 1; i < 5; i++) gh[(i - 1) * N + cc] = __float2half_rn(fluid ? g[i * N + cc] : 0.0f);
+  }
 }
 
 // Stored deviations <-> absolute populations f_i = dev_i + w_i n0.
@@ -821,18 +985,20 @@ __global__ void f_convert_kernel(const Inst* __restrict__ insts, int index, cons
 }  // namespace
 
 // ---------------------------------------------------------------------------
-size_t step_smem_bytes(int nthreads, int prefetch) {
-  return (size_t)(nthreads / 32) * (prefetch + 3) * kRowFloats * sizeof(float);
+size_t step_smem_bytes(int nthreads, int prefetch, bool h16) {
+  return (size_t)(nthreads / 32) * (prefetch + 3) * (h16 ? kRowWordsH : kRowFloats) * sizeof(float);
 }
+
+size_t state_bytes_f(const Inst& I) { return (size_t)I.nx * I.ny * 9 * (I.fp16 ? 2 : 4); }
+size_t state_bytes_g(const Inst& I) { return (size_t)I.nx * I.ny * (I.fp16 ? 12 : 20); }
 
 cudaError_t launch_init(const Inst* d_inst, const Inst& h, int index, cudaStream_t s) {
   dim3 blk(128), grd((h.nx + 127) / 128, h.ny);
   double* phi0 = reinterpret_cast<double*>(h.f[1]);  // f[1] is free before the first step
   init_phi_kernel<<<grd, blk, 0, s>>>(d_inst, index, phi0);
   init_pop_kernel<<<grd, blk, 0, s>>>(d_inst, index, phi0);
-  const size_t N = (size_t)h.nx * h.ny;
-  zero_kernel<<<256, 256, 0, s>>>(h.f[1], 9 * N);
-  zero_kernel<<<256, 256, 0, s>>>(h.g[1], 5 * N);
+  zero_kernel<<<256, 256, 0, s>>>(h.f[1], state_bytes_f(h) / 4);
+  zero_kernel<<<256, 256, 0, s>>>(h.g[1], state_bytes_g(h) / 4);
   return cudaGetLastError();
 }
 
@@ -867,22 +1033,32 @@ cudaError_t launch_f_import(const Inst* d_inst, const Inst& h, int index, const 
   return cudaGetLastError();
 }
 
-template <bool DIAG>
+cudaError_t launch_convert16(const Inst* d_inst, const Inst& h, int index, int parity, float* f,
+                             float* g, bool to_device_state, cudaStream_t s) {
+  dim3 blk(128), grd((h.nx + 127) / 128, h.ny);
+  if (to_device_state)
+    convert16_kernel<false><<<grd, blk, 0, s>>>(d_inst, index, parity, f, g);
+  else
+    convert16_kernel<true><<<grd, blk, 0, s>>>(d_inst, index, parity, f, g);
+  return cudaGetLastError();
+}
+
+template <bool DIAG, bool H>
 cudaError_t launch_step_p(const Inst* d_inst, const Item* d_items, int n_items, int nthreads,
                           int grid, const long long* d_t, int t_off, int prefetch, size_t smem,
                           cudaStream_t s) {
   switch (prefetch) {
     case 1:
-      step_kernel<DIAG, 1><<<grid, nthreads, smem, s>>>(d_inst, d_items, n_items, d_t, t_off);
+      step_kernel<DIAG, 1, H><<<grid, nthreads, smem, s>>>(d_inst, d_items, n_items, d_t, t_off);
       break;
     case 2:
-      step_kernel<DIAG, 2><<<grid, nthreads, smem, s>>>(d_inst, d_items, n_items, d_t, t_off);
+      step_kernel<DIAG, 2, H><<<grid, nthreads, smem, s>>>(d_inst, d_items, n_items, d_t, t_off);
       break;
     case 3:
-      step_kernel<DIAG, 3><<<grid, nthreads, smem, s>>>(d_inst, d_items, n_items, d_t, t_off);
+      step_kernel<DIAG, 3, H><<<grid, nthreads, smem, s>>>(d_inst, d_items, n_items, d_t, t_off);
       break;
     default:
-      step_kernel<DIAG, 4><<<grid, nthreads, smem, s>>>(d_inst, d_items, n_items, d_t, t_off);
+      step_kernel<DIAG, 4, H><<<grid, nthreads, smem, s>>>(d_inst, d_items, n_items, d_t, t_off);
       break;
   }
   return cudaGetLastError();
@@ -890,25 +1066,34 @@ cudaError_t launch_step_p(const Inst* d_inst, const Item* d_items, int n_items, 
 
 cudaError_t launch_step(const Inst* d_inst, const Item* d_items, int n_items, int nthreads,
                         int grid, const long long* d_t, int t_off, bool diag, int prefetch,
-                        cudaStream_t s) {
+                        bool h16, cudaStream_t s) {
   if (nthreads != kStepThreads || prefetch < 1 || prefetch > kMaxPrefetch)
     return cudaErrorInvalidValue;
   if (n_items <= 0) return cudaSuccess;
-  const size_t smem = step_smem_bytes(nthreads, prefetch);
-  return diag ? launch_step_p<true>(d_inst, d_items, n_items, nthreads, grid, d_t, t_off, prefetch,
-                                    smem, s)
-              : launch_step_p<false>(d_inst, d_items, n_items, nthreads, grid, d_t, t_off,
-                                     prefetch, smem, s);
+  const size_t smem = step_smem_bytes(nthreads, prefetch, h16);
+  if (h16)
+    return diag ? launch_step_p<true, true>(d_inst, d_items, n_items, nthreads, grid, d_t, t_off,
+                                            prefetch, smem, s)
+                : launch_step_p<false, true>(d_inst, d_items, n_items, nthreads, grid, d_t, t_off,
+                                             prefetch, smem, s);
+  return diag ? launch_step_p<true, false>(d_inst, d_items, n_items, nthreads, grid, d_t, t_off,
+                                           prefetch, smem, s)
+              : launch_step_p<false, false>(d_inst, d_items, n_items, nthreads, grid, d_t, t_off,
+                                            prefetch, smem, s);
 }
 
 int step_prefetch_for(int) { return 3; }
 
 cudaError_t set_step_smem_limit() {
-  const int lim = (int)step_smem_bytes(kStepThreads, kMaxPrefetch);
+  const int lim = (int)step_smem_bytes(kStepThreads, kMaxPrefetch, false);
   cudaError_t e = cudaSuccess;
-#define SET_LIM(DG, PF)                                                                      \
-  if (e == cudaSuccess)                                                                      \
-    e = cudaFuncSetAttribute(step_kernel<DG, PF>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+#define SET_LIM(DG, PF)                                                                         \
+  if (e == cudaSuccess)                                                                         \
+    e = cudaFuncSetAttribute(step_kernel<DG, PF, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                             lim);                                                              \
+  if (e == cudaSuccess)                                                                         \
+    e = cudaFuncSetAttribute(step_kernel<DG, PF, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                             lim);
   SET_LIM(true, 1) SET_LIM(false, 1) SET_LIM(true, 2) SET_LIM(false, 2)
   SET_LIM(true, 3) SET_LIM(false, 3) SET_LIM(true, 4) SET_LIM(false, 4)
 #undef SET_LIM

@@ -247,13 +247,15 @@ def outcomes_from_history(hist, after=(0, 100)):
     return np.array([tb, hist[sel, 8].mean(), hist[sel, 6].mean(), hist[sel, 9].mean()])
 
 
-def lbm_outcomes(rows, steps=5000, stream=None, chunk=1024):
+def lbm_outcomes(rows, steps=5000, stream=None, chunk=1024, precision=0):
     """Run every input row as a lattice of the batched LBM path for `steps`
-    steps; returns outcomes [n][4] (NaN rows: no breakup in time)."""
+    steps; returns outcomes [n][4] (NaN rows: no breakup in time).
+    precision 1 stores the populations in FP16 (offsets)."""
     out = np.empty((len(rows), N_OUT))
     for a in range(0, len(rows), chunk):
         part = rows[a:a + chunk]
-        h = ij.ij_create([lattice_params(r) for r in part], stream=stream)
+        h = ij.ij_create([dict(lattice_params(r), precision=precision) for r in part],
+                         stream=stream)
         ij.ij_step(h, steps)
         for k in range(len(part)):
             out[a + k] = outcomes_from_history(ij.ij_history(h, k))

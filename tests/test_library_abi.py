@@ -29,6 +29,7 @@ def _raw_create(p, count=1):
     dict(width_W=-1.0), dict(tau_phi=0.0), dict(nu_air=0.0), dict(theta_deg=181.0),
     dict(geometry=7), dict(axial_bc=5), dict(init_kind=9), dict(precision=3),
     dict(nozzle_width=60, wall_thickness=4), dict(T1=-1), dict(diag_every=-1),
+    dict(precision=1, nx=63),  # 2-D FP16 storage pairs columns: nx must be even
 ])
 def test_invalid_parameters_are_rejected_on_the_host(bad):
     p = dict(W.cfg1(), **bad)

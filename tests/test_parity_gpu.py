@@ -95,6 +95,16 @@ def test_ragged_and_degenerate_sizes(ij, nx, ny):
     _one_step_case(ij, p, steps=3, tol=1e-5)
 
 
+@pytest.mark.parametrize("cx", [26, 27, 28, 29, 30])
+def test_wall_on_strip_edges(ij, cx):
+    """Nozzle walls on the edge lanes of the 28-column strips (at cx = 30
+    all four edge-lane cases: wall column inside the strip, fluid outside)."""
+    nx = 84
+    p = W.small_nozzle(nx=nx, ny=40, nozzle_width=nx - 2 * cx, nozzle_length=20,
+                       wall_thickness=4)
+    _one_step_case(ij, p, steps=3, tol=1e-5)
+
+
 def test_cfg1_1000_steps_density_and_order_parameter(ij):
     """cfg 1 as specified (nominal drive): n after 1000 steps within 1e-5
     relative L-infinity of the FP64 oracle (scaled by max n), phi within
