@@ -250,7 +250,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kStepBlocksPerSM)
   constexpr int D = P + 3;  // ring rows: R+P .. R-2 are live
   constexpr int kRowW = H ? kRowWordsH : kRowFloats;
   extern __shared__ float4 smem4[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // with one warp per block the warp index is the constant 0, so the compiler
+  // sees the work item, its lattice and the row loop as warp-uniform
+  const int lane = threadIdx.x & 31, warp = kWarpsPerBlock == 1 ? 0 : threadIdx.x >> 5;
   // FP32: each lane's column of the ring; FP16: the warp's ring
   float* ring = reinterpret_cast<float*>(smem4) + warp * D * kRowW + (H ? 0 : lane);
   const unsigned ring_sa = (unsigned)__cvta_generic_to_shared(ring);
@@ -465,7 +467,14 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kStepBlocksPerSM)
         const float sW = __shfl_up_sync(kFull, pe2, 1), sE = __shfl_down_sync(kFull, pe2, 1);
         // diagnostics of this cell: ink weight e, e n, e n u_y, n, phi, n u_y
         float dg[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (k >= 4 && col_lane && k2 == 0) {
+        // Every lane runs the collision (no divergent branch, so the
+        // collision and the streaming below form one block the compiler can
+        // interleave); only lanes with a fluid cell that is pulled from
+        // (cvalid) raise the flag or count in the diagnostics.  The results
+        // of the other lanes are never read: a fluid cell pulling from a
+        // solid one takes its own bounce-back value instead.
+        const bool cvalid = col_lane && k2 == 0;
+        if (k >= 4) {
           int s2 = sl - 2;
           if (s2 < 0) s2 += D;
           const float* sg = ring + s2 * kRowW;
@@ -495,7 +504,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kStepBlocksPerSM)
           const float inv_n = __frcp_rn(n);  // 1 / n, correctly rounded
           const float ux = (mx + 0.5f * Fx) * inv_n, uy = (my + 0.5f * Fy) * inv_n;
           const float u2 = ux * ux + uy * uy;
-          if (!(u2 < 0.09f)) atomicOr(I.status, kStatusNumeric);
+          if (cvalid && !(u2 < 0.09f)) atomicOr(I.status, kStatusNumeric);
           const float om = __frcp_rn(0.5f + 3.0f * (nu_air + C * dnu));
           const float pref = 3.0f * (1.0f - 0.5f * om);
           // A_i - n0 = 3 (phi mu + n / 3) - n0 for i >= 1 (Eq. 6), on deviations
@@ -555,7 +564,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kStepBlocksPerSM)
           // sum_{i>=1} g_i the relaxation uses small terms only
           on[0] = fs[0];
           on[1] = g2[0] + ((g2[1] + g2[2] + g2[3] + g2[4]) - sum_ge) * inv_tphi;
-          if (DIAG && out_lane && Rc >= y0 && Rc < y0 + ch) {
+          if (DIAG && cvalid && out_lane && Rc >= y0 && Rc < y0 + ch) {
             const float e = fminf(fmaxf(phi * inv_phis, 0.0f), 1.0f);
             dg[0] = e;
             dg[1] = e * n;
@@ -589,7 +598,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kStepBlocksPerSM)
         const float w8 = __shfl_up_sync(kFull, cn[7], 1), wP1 = __shfl_up_sync(kFull, cB[8], 1);
         const float e3 = __shfl_down_sync(kFull, cB[2], 1), e6 = __shfl_down_sync(kFull, cA[2], 1);
         const float e7 = __shfl_down_sync(kFull, cn[6], 1), eP3 = __shfl_down_sync(kFull, cB[10], 1);
-        if (k >= 6 && out_lane && k3 == 0) {
+        const bool svalid = out_lane && k3 == 0;
+        if (k >= 6) {
           const int Y = R - 3;
           float fn[9];
           fn[0] = oB[0];
@@ -602,7 +612,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kStepBlocksPerSM)
           fn[7] = e7;
           fn[8] = w8;
           float P1 = wP1, P2 = cA[3], P3 = eP3, P4 = cn[11];
-          if (near_solid_v(geom, bc, ny, L, wt, colwall, Y)) {
+          if (svalid && near_solid_v(geom, bc, ny, L, wt, colwall, Y)) {
             // halfway bounce-back: a population whose source is solid is the
             // cell's own post-collision population of the opposite direction
             const unsigned sm = solid_sources(I, x, Y);
@@ -617,7 +627,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kStepBlocksPerSM)
               if (sm & (1u << 8)) fn[8] = cB[5];
             }
           }
-          if (!H) {
+          if (svalid && !H) {
             float* fo = fout + Y * nx + x;
             float* go = gout + Y * nx + x;
 #pragma unroll
@@ -627,7 +637,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kStepBlocksPerSM)
             go[2 * N] = oB[3] + P2;
             go[3 * N] = oB[4] + P3;
             go[4 * N] = oB[5] + P4;
-          } else {
+          } else if (svalid) {
             // round to nearest even on store
             __half* fo = fhout + Y * nx + x;
             __half* go = ghout + Y * nx + x;
