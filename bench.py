@@ -29,9 +29,13 @@ METRIC = "MLUPS & %HBM peak, plain vs batched/FP16-store LBM; surrogate speedup 
 BYTES_PER_LUP = {"2d": 112, "2d16": 60, "3d32": 208, "3d16": 108}
 FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes per step-kernel launch from an ncu capture (dram__bytes_read.sum
-# + dram__bytes_write.sum) of the workload below, valid only for the kernel
-# source whose sha256 prefix is recorded with it.
-NCU_TRAFFIC = {}
+# + dram__bytes_write.sum, mean of two launches without diagnostics) of the
+# workload, valid only for the kernel source whose sha256 prefix and the row
+# chunk are recorded with it.
+NCU_TRAFFIC = {
+    "cfg2": {"kernel_sha": "1fdcbd5973e35985", "chunk": 24, "bytes_per_step": 749.33e6},
+    "cfg2h": {"kernel_sha": "1fdcbd5973e35985", "chunk": 24, "bytes_per_step": 369.84e6},
+}
 
 
 def kernel_hash(params):
@@ -312,7 +316,8 @@ def run_native(args):
         achieved = bpl * cells / (per_step_ms / 1e3) / 1e9
         traffic = None
         rec = NCU_TRAFFIC.get(args.workload)
-        if rec and rec.get("kernel_sha") == kernel_hash(params):
+        if (rec and rec.get("kernel_sha") == kernel_hash(params)
+                and all(b["chunk"] == rec["chunk"] for b in tuning)):
             traffic = rec["bytes_per_step"]
         line = {
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
