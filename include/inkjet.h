@@ -128,7 +128,10 @@ typedef struct {
   double droplet_velocity;   /* e n-weighted mean u_y over the leading run */
   double satellites;         /* runs starting at or above y = L, minus one */
   double runs;
-  double reserved;
+  double head_y, tail_y;     /* where w crosses 1/2 at the upper / lower end of the
+                                leading run, interpolated between rows (-1: no run);
+                                head and tail velocities are their differences
+                                between records */
 } ij_obs;
 
 /* Device-memory allocator callbacks; NULL selects cudaMalloc / cudaFree. */
@@ -171,7 +174,7 @@ ij_status ij_step(ij_handle h, long long nsteps);
 ij_status ij_observe(ij_handle h, int index, ij_obs* out, float* phi_out, int phi_on_device);
 
 /* ij_history -- copy up to max_records diagnostics records of lattice
- * `index` (oldest first, 12 doubles each in ij_obs order) into host memory
+ * `index` (oldest first, 13 doubles each in ij_obs order) into host memory
  * `out` (may be NULL); *count receives the number of records held. */
 ij_status ij_history(ij_handle h, int index, double* out, int max_records, int* count);
 
@@ -246,7 +249,7 @@ ij_status ij_get_tuning(ij_handle h, int bucket, int* block_size, int* chunk, in
  *                   Same [i][y][x] order as above.  Read only.
  *   f_out, g_out  : device, receive the state at t+1 (solid cells untouched);
  *                   must not alias the inputs.
- *   record_out    : device, 12 doubles (ij_obs order) receiving the
+ *   record_out    : device, 13 doubles (ij_obs order) receiving the
  *                   diagnostics record of the state at t, or NULL for none.
  *                   Each call starts a fresh breakup history, so breakup_step
  *                   is t when the neck is already closed, else -1.

@@ -347,6 +347,14 @@ static void diagnose(orc3* s, long long t) {
   rec[8] = mm > 0 ? pp / mm : 0.0;
   rec[9] = nabove > 1 ? nabove - 1 : 0;
   rec[10] = nruns;
+  /* head and tail of the leading droplet along z, as in the 2-D oracle */
+  rec[11] = rec[12] = -1.0;
+  if (lead0 >= 0) {
+    int top = lead1 - 1;
+    rec[11] = lead1 < nz ? top + (s->wrow[top] - 0.5) / (s->wrow[top] - s->wrow[lead1]) : top;
+    rec[12] = lead0 > 0 ? lead0 - (s->wrow[lead0] - 0.5) / (s->wrow[lead0] - s->wrow[lead0 - 1])
+                        : lead0;
+  }
   if (s->nhist == s->caphist) {
     s->caphist *= 2;
     s->hist = realloc(s->hist, (size_t)s->caphist * ORC_REC * sizeof(double));

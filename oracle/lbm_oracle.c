@@ -584,7 +584,11 @@ void orc_stream_only(orc_sim* s, const double* fin, const double* gin, double* f
  * neck row is vanishing), its time interpolated linearly in the neck width
  * between this record and the previous one.  The leading droplet is the highest run (volume, centroid,
  * e n-weighted velocity); satellites = (runs that start at or above the
- * nozzle exit) - 1. */
+ * nozzle exit) - 1.  Its head and tail are where w(y) crosses 1/2 at the
+ * run's upper and lower ends, by linear interpolation between the last row
+ * inside and the first row outside (the end row itself at the lattice's
+ * edge; -1 without a run); their velocities are differences between
+ * records. */
 #define NECK_BREAK 0.01
 
 static void diagnose(orc_sim* s, long long t) {
@@ -659,6 +663,13 @@ static void diagnose(orc_sim* s, long long t) {
   rec[8] = mm > 0 ? pp / mm : 0.0;
   rec[9] = nabove > 1 ? nabove - 1 : 0;
   rec[10] = nruns;
+  rec[11] = rec[12] = -1.0;
+  if (lead0 >= 0) {
+    int top = lead1 - 1;
+    rec[11] = lead1 < ny ? top + (s->wrow[top] - 0.5) / (s->wrow[top] - s->wrow[lead1]) : top;
+    rec[12] = lead0 > 0 ? lead0 - (s->wrow[lead0] - 0.5) / (s->wrow[lead0] - s->wrow[lead0 - 1])
+                        : lead0;
+  }
   if (s->nhist == s->caphist) {
     s->caphist *= 2;
     s->hist = realloc(s->hist, (size_t)s->caphist * ORC_REC * sizeof(double));

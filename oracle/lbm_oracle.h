@@ -61,7 +61,7 @@ typedef struct {
 typedef struct orc_sim orc_sim;
 
 /* number of doubles in one diagnostics record */
-#define ORC_REC 12
+#define ORC_REC 13
 
 orc_sim* orc_create(const orc_params* p);
 void orc_destroy(orc_sim* s);

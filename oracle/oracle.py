@@ -10,7 +10,7 @@ import numpy as np
 from . import build as _build
 
 REC_FIELDS = ("t", "mass_n", "mass_phi", "mom_y", "neck", "breakup", "volume",
-              "centroid_y", "velocity", "satellites", "runs", "reserved")
+              "centroid_y", "velocity", "satellites", "runs", "head_y", "tail_y")
 
 
 class _Params(C.Structure):

@@ -152,6 +152,8 @@ struct ij_handle_s {
   }
 };
 
+static_assert(sizeof(ij_obs) == kRec * sizeof(double), "ij_obs is one diagnostics record");
+
 namespace {
 
 ij_status validate(const ij_params& p, int k) {

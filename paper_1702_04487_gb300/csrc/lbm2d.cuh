@@ -12,7 +12,7 @@ enum { GEOM_NONE = 0, GEOM_NOZZLE = 1, GEOM_PLATE = 2 };
 enum { BC_ZG = 0, BC_PER = 1, BC_CLOSED = 2 };
 enum { INIT_MENISCUS = 0, INIT_DROP = 1, INIT_FLAT = 2, INIT_UNIFORM = 3 };
 
-constexpr int kRec = 12;        // doubles per diagnostics record
+constexpr int kRec = 13;        // doubles per diagnostics record
 constexpr int kHistCap = 1024;  // records kept per lattice (ring)
 constexpr unsigned kStatusNumeric = 1u;
 

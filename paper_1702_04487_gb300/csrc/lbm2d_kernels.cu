@@ -913,7 +913,14 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(const Inst* __res
     rec[8] = mm > 0 ? pp / mm : 0.0;
     rec[9] = nabove > 1 ? nabove - 1 : 0;
     rec[10] = nruns;
-    rec[11] = 0.0;
+    // head and tail of the leading run: where w crosses 1/2 at its ends,
+    // interpolated between the last row inside and the first row outside
+    rec[11] = rec[12] = -1.0;
+    if (lead0 >= 0) {
+      const int top = lead1 - 1;
+      rec[11] = lead1 < ny ? top + (w[top] - 0.5) / (w[top] - w[lead1]) : (double)top;
+      rec[12] = lead0 > 0 ? lead0 - (w[lead0] - 0.5) / (w[lead0] - w[lead0 - 1]) : (double)lead0;
+    }
     st[4] = (double)(cnt + 1);
     I.sums[0] = I.sums[1] = I.sums[2] = I.sums[3] = 0.0;
   }

@@ -19,7 +19,7 @@ from . import build as _build
 
 IJ_OK, IJ_ERR_PARAM, IJ_ERR_CUDA, IJ_ERR_NUMERIC, IJ_ERR_TIMEOUT, IJ_ERR_STATE, IJ_ERR_OOM = range(7)
 REC_FIELDS = ("step", "mass_n", "mass_phi", "mom_y", "neck", "breakup_step", "droplet_volume",
-              "droplet_centroid_y", "droplet_velocity", "satellites", "runs", "reserved")
+              "droplet_centroid_y", "droplet_velocity", "satellites", "runs", "head_y", "tail_y")
 HEADER = os.path.join(_build.ROOT, "include", "inkjet.h")
 
 

@@ -97,6 +97,24 @@ def big_nozzle(nx=2048, ny=8192):
                 diag_every=10)
 
 
+def e1(F0=2e-3, **kw):
+    """The paper's ejection set-up at its own lattice parameters ("Reproducing
+    the experiment"): 200 x 800 lattice, nozzle 80 wide (radius 40) and 120
+    long, density ratio 1000 (phi* = 499.5), W = 3, tau_n = 0.85 in both
+    fluids, tau_phi = 0.8, surface tension 1.08, wall angle 90 degrees, and
+    the 5 / 3 us positive / negative pulses as 3050 / 1830 steps without
+    repetition.  The wall thickness (10) and the drive amplitude are not
+    printed; the negative pulse is F0 / 2 as in the sweeps."""
+    nu = (0.85 - 0.5) / 3.0
+    p = dict(nx=200, ny=800, geometry=GEOM_NOZZLE, nozzle_width=80, nozzle_length=120,
+             wall_thickness=10, rho_ink=1000.0, rho_air=1.0, nu_ink=nu, nu_air=nu, sigma=1.08,
+             width_W=3.0, tau_phi=0.8, gamma=0.0, theta_deg=90.0, F0=F0, F_neg=F0 / 2,
+             T1=3050, T2=1830, T_idle=0, axial_bc=BC_ZERO_GRADIENT, init_kind=INIT_MENISCUS,
+             jitter=1e-6, seed=11, diag_every=100)
+    p.update(kw)
+    return p
+
+
 def small_nozzle(nx=48, ny=96, **kw):
     """A small nozzle lattice for quick checks (16 wide, 30 long, walls 3)."""
     p = dict(nx=nx, ny=ny, geometry=GEOM_NOZZLE, nozzle_width=16, nozzle_length=30,

@@ -144,3 +144,28 @@ def test_fp32_noise_floor_of_small_nozzle3():
                         g * (1 + eps * rng.uniform(-1, 1, g.shape)), t)
     d = np.abs(noisy.state()[1].sum(0) - ref.state()[1].sum(0)).max() / 4.5
     assert 5e-6 < d < 3e-5
+
+
+def test_head_and_tail_closed_form_along_z():
+    """Head and tail of the leading run of planes along z, as in 2-D: a slab
+    of ink over planes 5..9 of a 3 x 2 box (plane ink weight 6), with a
+    plane of e = 0.05 (weight 0.3) above it."""
+    nx, ny, nz = 3, 2, 16
+    p = {k: v for k, v in W.small_nozzle3(nx=nx, ny=ny, nz=nz, geometry=W.GEOM_NONE,
+                                          axial_bc=W.BC_PERIODIC, init_kind=W.INIT_UNIFORM,
+                                          init_r=-4.5, diag_every=1).items()
+         if k not in ("dim", "precision")}
+    s = OracleSim3(p)
+    w = lattice3()[3]
+    n0 = 5.5
+    f = np.broadcast_to(w[:, None, None, None] * n0, (19, nz, ny, nx)).copy()
+    g = np.zeros((7, nz, ny, nx))
+    phi = np.full(nz, -4.5)
+    phi[5:10] = 4.5
+    phi[10] = 0.05 * 4.5
+    g[0] = phi[:, None, None]
+    s.set_state(f, g, 0)
+    s.step(1)
+    r = s.history()[0]
+    assert r[10] == 1
+    assert abs(r[11] - (9 + 5.5 / 5.7)) < 1e-12 and abs(r[12] - (5 - 5.5 / 6)) < 1e-12

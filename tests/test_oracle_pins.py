@@ -185,6 +185,22 @@ def test_momentum_budget_of_uniform_driven_box():
     assert np.allclose(h[:, 3], expect, rtol=1e-12, atol=1e-16)
 
 
+def test_momentum_budget_of_repeated_waveform():
+    """The same budget with T_idle > 0: the positive / negative / idle cycle
+    repeats with period T1 + T2 + T_idle (Fig. 1 as a periodic waveform)."""
+    p = W.small_nozzle(nx=12, ny=10, geometry=W.GEOM_NONE, axial_bc=W.BC_PERIODIC,
+                       init_kind=W.INIT_UNIFORM, init_r=4.5, F0=1e-4, F_neg=4e-5, T1=7, T2=5,
+                       T_idle=4, diag_every=1)
+    s = OracleSim(p)
+    s.step(40)
+    h = s.history()
+    cycle = [1e-4] * 7 + [-4e-5] * 5 + [0.0] * 4
+    F = np.array((cycle * 3)[:40])
+    N = p["nx"] * p["ny"]
+    expect = (np.concatenate([[0.0], np.cumsum(F)[:-1]]) + F / 2) * N
+    assert np.allclose(h[:, 3], expect, rtol=1e-12, atol=1e-16)
+
+
 def test_uniform_state_is_stationary_under_zero_gradient_ends():
     """A uniform fluid at rest stays uniform to round-off with the
     'fully developed' (zero-gradient) axial ends."""
@@ -394,3 +410,46 @@ def test_fp32_noise_floor_of_cfg1():
                         g * (1 + eps * rng.uniform(-1, 1, g.shape)), t)
     d = np.abs(noisy.state()[1].sum(0) - ref.state()[1].sum(0)).max() / 4.5
     assert 2e-6 < d < 1.5e-5
+
+
+# ------------------------------------------------------- head and tail
+def _slab_record(rows_phi, nx=4):
+    """Diagnostics record of a state at rest whose order parameter is
+    phi(y) = rows_phi[y] in every column (no walls, periodic)."""
+    ny = len(rows_phi)
+    p = W.small_nozzle(nx=nx, ny=ny, geometry=W.GEOM_NONE, axial_bc=W.BC_PERIODIC,
+                       init_kind=W.INIT_UNIFORM, init_r=-4.5, diag_every=1)
+    n0 = 0.5 * (p["rho_ink"] + p["rho_air"])
+    wts = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    f = np.broadcast_to(wts[:, None, None] * n0, (9, ny, nx)).copy()
+    g = np.zeros((5, ny, nx))
+    g[0] = np.asarray(rows_phi, dtype=np.float64)[:, None]
+    s = OracleSim(p)
+    s.set_state(f, g, 0)
+    s.step(1)
+    return s.history()[0]
+
+
+def test_head_and_tail_closed_form():
+    """Head and tail of the leading run (rows with more than half a cell of
+    ink) where the row ink weight crosses 1/2, interpolated between rows:
+    on slabs of 4 columns they have closed forms."""
+    ps = 4.5
+    ink, air = ps, -ps
+    # sharp slab over rows 6..11: w = 4 inside, 0 outside
+    r = _slab_record([air] * 6 + [ink] * 6 + [air] * 8)
+    assert r[10] == 1
+    assert abs(r[11] - (11 + 3.5 / 4)) < 1e-12 and abs(r[12] - (6 - 3.5 / 4)) < 1e-12
+    # partial rows outside: w = 0.4 above (e = 0.1), 0.2 below (e = 0.05)
+    r = _slab_record([air] * 5 + [0.05 * ps] + [ink] * 6 + [0.1 * ps] + [air] * 7)
+    assert abs(r[11] - (11 + 3.5 / 3.6)) < 1e-12 and abs(r[12] - (6 - 3.5 / 3.8)) < 1e-12
+    # two runs: the leading droplet is the higher one (rows 10..13)
+    r = _slab_record([air] * 2 + [ink] * 3 + [air] * 5 + [ink] * 4 + [air] * 6)
+    assert r[10] == 2
+    assert abs(r[11] - (13 + 3.5 / 4)) < 1e-12 and abs(r[12] - (10 - 3.5 / 4)) < 1e-12
+    # a run reaching the top row ends there
+    r = _slab_record([air] * 14 + [ink] * 6)
+    assert r[11] == 19 and abs(r[12] - (14 - 3.5 / 4)) < 1e-12
+    # no run
+    r = _slab_record([air] * 12)
+    assert r[10] == 0 and r[11] == -1 and r[12] == -1

@@ -80,6 +80,13 @@ def test_boundaries_and_geometries(ij, bc, geom):
     _one_step_case(ij, p, steps=5, tol=1e-5)
 
 
+def test_repeated_waveform(ij):
+    """T_idle > 0 repeats the positive / negative / idle cycle: 130 steps
+    over three periods of 45, every population against the oracle."""
+    p = W.small_nozzle(T1=20, T2=15, T_idle=10, F0=2e-3, F_neg=1.5e-3)
+    _one_step_case(ij, p, steps=130, tol=1e-5)
+
+
 @pytest.mark.parametrize("nx,ny", [(37, 53), (1, 7), (5, 2), (3, 1), (300, 41), (513, 19),
                                    (256, 30), (257, 30)])
 def test_ragged_and_degenerate_sizes(ij, nx, ny):
@@ -123,6 +130,25 @@ def test_cfg1_1000_steps_density_and_order_parameter(ij):
     no, po = _fields_from_state(fo, go)
     assert _rel(ng, no, np.abs(no).max()) < 1e-5
     assert _rel(pg, po, 4.5) < 3e-5
+
+
+def test_e1_paper_lattice_parameters_100_steps(ij):
+    """The paper's own lattice parameters (200 x 800, density ratio 1000 so
+    phi* = 499.5 and n0 = 500.5, tau 0.85, sigma 1.08, 90 degrees): FP32
+    storage of values near 500 against the FP64 oracle after 100 steps of the
+    positive pulse; n within 1e-5 of max n, phi within 3e-5 of phi*."""
+    p = W.e1(F0=1.5e-2)
+    h = ij.ij_create(p)
+    ij.ij_step(h, 100)
+    fg, gg = ij.ij_get_state(h, 0)
+    o = OracleSim(p)
+    o.step(100)
+    fo, go = o.state()
+    ng, pg = _fields_from_state(fg.astype(np.float64), gg.astype(np.float64))
+    no, po = _fields_from_state(fo, go)
+    assert _rel(ng, no, np.abs(no).max()) < 1e-5
+    assert _rel(pg, po, 499.5) < 3e-5
+    assert _rel(fg, fo, np.abs(fo).max()) < 1e-5
 
 
 def test_cfg1_ejecting_1000_steps(ij):
@@ -169,6 +195,32 @@ def test_cfg1_full_run_breakup_and_velocity(ij):
     assert np.abs(hist_g[:, 6] - hist_o[:, 6]).max() < 1e-3 * hist_o[:, 6].max()
     fo, go = o.state()
     assert _rel(phi, go.sum(0) * (o.kinds() == 0), 4.5) < 1e-4
+
+
+def test_cfg1_head_and_tail_after_breakup(ij):
+    """Head and tail of the leading droplet (where the row ink weight
+    crosses 1/2 at its ends) over cfg 1's 4000-step run: their velocities
+    over the records after pinch-off (differences of positions between the
+    first and the last of them) within 2 % of the oracle's, their final
+    positions within one row.  The droplet drifts by under one row in that
+    window, so FP32 noise of ~1e-3 rows in a position is a few tenths of a
+    percent of the difference."""
+    p = W.cfg1()
+    h = ij.ij_create(p)
+    ij.ij_step(h, 4000)
+    hg = ij.ij_history(h, 0)
+    o = OracleSim(p)
+    o.step(4000)
+    ho = o.history()
+    tb = ho[-1, 5]
+    k0 = int(np.searchsorted(ho[:, 0], tb)) + 1  # first record after pinch-off
+    assert len(ho) - k0 >= 10, "the run must continue past pinch-off"
+    for col in (11, 12):
+        vo = (ho[-1, col] - ho[k0, col]) / (ho[-1, 0] - ho[k0, 0])
+        vg = (hg[-1, col] - hg[k0, col]) / (hg[-1, 0] - hg[k0, 0])
+        assert vo > 0 and abs(vg - vo) <= 0.02 * vo, (col, vg, vo)
+        assert abs(hg[-1, col] - ho[-1, col]) < 1.0
+    assert ho[-1, 11] > ho[-1, 12] >= p["nozzle_length"]  # a droplet above the nozzle exit
 
 
 @pytest.mark.parametrize("bc", [W.BC_PERIODIC, W.BC_CLOSED])

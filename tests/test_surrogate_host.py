@@ -27,7 +27,7 @@ def test_lattice_of_an_input_row():
 
 def _history(tb, t_end=2000, every=10):
     t = np.arange(0, t_end + 1, every, dtype=float)
-    h = np.zeros((len(t), 12))
+    h = np.zeros((len(t), 13))
     h[:, 0] = t
     h[:, 5] = np.where(t >= tb, tb, -1.0) if tb > 0 else -1.0
     h[:, 6] = 1000.0 + t          # volume

@@ -36,7 +36,7 @@ def test_noalloc_step_matches_handle_step_twice():
     dev = np.where(fluid[None], f_abs - WEIGHTS[:, None, None] * n0, 0.0).astype(np.float32)
     bufs_f = [torch.from_numpy(dev).cuda(), torch.zeros_like(torch.from_numpy(dev)).cuda()]
     bufs_g = [torch.from_numpy(g).cuda(), torch.zeros_like(torch.from_numpy(g)).cuda()]
-    rec = torch.zeros(12, dtype=torch.float64, device="cuda")
+    rec = torch.zeros(13, dtype=torch.float64, device="cuda")  # one record (ij_obs)
     params = inkjet.make_params(p)
     stream = torch.cuda.current_stream().cuda_stream
 
@@ -63,7 +63,8 @@ def test_noalloc_step_matches_handle_step_twice():
         if t == 0:
             obs, _ = inkjet.ij_observe(h, 0, phi=False)
             assert obs["step"] == 0
-            for key, col in (("mass_n", 1), ("mass_phi", 2), ("droplet_volume", 6)):
+            for key, col in (("mass_n", 1), ("mass_phi", 2), ("droplet_volume", 6),
+                             ("head_y", 11), ("tail_y", 12)):
                 assert abs(r[col] - obs[key]) <= 1e-6 * max(1.0, abs(obs[key]))
 
 
