@@ -173,7 +173,11 @@ __device__ __forceinline__ float drive3(const Inst3& I, long long t) {
 // Collision of the planes [zfirst, zlast) of a 32 x 4 column tile; the block
 // marches up z and keeps phi of planes z-1, z, z+1 of the tile (with a
 // one-cell halo) in shared memory, so that the D3Q19 stencil of a fluid cell
-// away from walls reads shared memory only.
+// away from walls reads shared memory only.  The ring has four slots (plane
+// zz in slot zz & 3): the plane loaded at the start of an iteration goes to
+// the slot of plane z-2, which no warp still reads once every warp has
+// passed the previous iteration's barrier, so one barrier per plane
+// suffices.
 constexpr int kZChunk = 8;
 constexpr int kTX = 32, kTY = 4;
 
@@ -181,7 +185,7 @@ template <bool H, bool DIAG>
 __global__ void __launch_bounds__(128) collide3_kernel(const Inst3* __restrict__ insts, int index,
                                                        const long long* __restrict__ d_t,
                                                        int t_off) {
-  __shared__ float tile[3][kTY + 2][kTX + 2];
+  __shared__ float tile[4][kTY + 2][kTX + 2];
   __shared__ float red[4][6];
   const Inst3& I = insts[index];
   // a lattice whose numeric flag is set is frozen; one read per block keeps
@@ -203,14 +207,14 @@ __global__ void __launch_bounds__(128) collide3_kernel(const Inst3* __restrict__
   const bool inxy = x < I.nx && y < I.ny;
   // phi of plane zz (extended index) into its ring slot, with the tile's halo
   auto load_plane = [&](int zz) {
-    const int slot = ((zz % 3) + 3) % 3;
+    const int slot = zz & 3;
     int zm = 0;
     const bool ok = map_z(I, zz, zm);
     for (int idx = tid; idx < (kTY + 2) * (kTX + 2); idx += kTX * kTY) {
-      const int lx = idx % (kTX + 2), ly = idx / (kTX + 2);
-      int gx = ((int)blockIdx.x * kTX + lx - 1) % I.nx, gy = ((int)blockIdx.y * kTY + ly - 1) % I.ny;
-      if (gx < 0) gx += I.nx;
-      if (gy < 0) gy += I.ny;
+      const int lx = idx % (kTX + 2), ly = idx / (kTX + 2);  // constant divisors
+      // the tile's columns and rows lie within one period of the lattice
+      const int gx = wrap3((int)blockIdx.x * kTX + lx - 1, I.nx);
+      const int gy = wrap3((int)blockIdx.y * kTY + ly - 1, I.ny);
       tile[slot][ly][lx] = ok ? I.phi[cell3(I, gx, gy, zm)] : 0.0f;
     }
   };
@@ -245,7 +249,7 @@ __global__ void __launch_bounds__(128) collide3_kernel(const Inst3* __restrict__
         if (ns && kind_at3(I, xn, yn, zn) != 0)
           pn = ghost3(I, xn, yn, zn);
         else
-          pn = tile[((zn % 3) + 3) % 3][threadIdx.y + 1 + ey3(i)][threadIdx.x + 1 + ex3(i)];
+          pn = tile[zn & 3][threadIdx.y + 1 + ey3(i)][threadIdx.x + 1 + ex3(i)];
         lap += 6.0f * w3(i) * (pn - phi);
         gx += 3.0f * w3(i) * (float)ex3(i) * pn;
         gy += 3.0f * w3(i) * (float)ey3(i) * pn;
@@ -338,7 +342,6 @@ __global__ void __launch_bounds__(128) collide3_kernel(const Inst3* __restrict__
         atomicAdd(I.sums + 2, s[5]);
       }
     }
-    __syncthreads();  // the slot of plane z-1 is refilled with plane z+2 next
   }
 }
 
