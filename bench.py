@@ -370,7 +370,8 @@ def run_surrogate(args):
     y_tr = S.lbm_outcomes(x_tr, steps=steps)
     t_gen = time.perf_counter() - t0
     ok = S.finite_rows(y_tr)
-    sg = S.Surrogate(members=5, hidden=256, batch=256, seed=5, lr=1e-3)
+    members, hidden = 5, 256
+    sg = S.Surrogate(members=members, hidden=hidden, batch=256, seed=5, lr=1e-3)
     sg.set_data(x_tr[ok], y_tr[ok])
     t0 = time.perf_counter()
     loss = sg.train(args.sg_train_steps)
@@ -404,6 +405,29 @@ def run_surrogate(args):
     for _ in range(10):
         sg.predict(x_ev, gate=True)
     t_pred = (time.perf_counter() - t0) / 10
+    # gated queries by batch size, host arrays in and out (one tenth of each
+    # batch has a contact angle beyond the input box, which the gate must
+    # reject); the forward pass is 2 (7 H + 3 H^2 + 4 H) FLOP per member and
+    # query, on BF16 tensor cores
+    flop_q = 2.0 * members * (7 * hidden + 3 * hidden * hidden + 4 * hidden)
+    rng = np.random.default_rng(47)
+    latency = []
+    for B in (1, 64, 4096, 65536):
+        xb = S.sample_inputs(B, 1000 + B)
+        n_out = B // 10
+        if n_out:
+            xb[:n_out, 0] = rng.uniform(160.0, 175.0, n_out)
+        sg.predict(xb, gate=True)  # workspace for this size
+        ts = []
+        for _ in range(20):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, _, a = sg.predict(xb, gate=True)
+            ts.append(time.perf_counter() - t0)
+        med = statistics.median(ts)
+        latency.append({"batch": B, "median_ms": med * 1e3, "queries_per_s": B / med,
+                        "tflops": flop_q * B / med / 1e12, "accepted": int(a.sum()),
+                        "out_of_box_accepted": int(a[:n_out].sum())})
     # accuracy / acceptance trade-off of the spread thresholds (same
     # predictions, thresholds applied to the returned spreads; the LBM cost
     # of the rejected queries is taken at the batched rate)
@@ -452,6 +476,7 @@ def run_surrogate(args):
             "breakup_p95": float(np.percentile(e16_tb, 95)) if len(e16_tb) else None,
             "velocity_p95": float(np.percentile(e16_v, 95)) if len(e16_v) else None},
         "surrogate_only_queries_per_s": n / t_pred,
+        "query_latency": latency,
         "accepted": int(acc.sum()), "accepted_ejecting": int(sel.sum()),
         "accepted_not_ejecting": int((acc & ~fin).sum()),
         "error_accepted": {
