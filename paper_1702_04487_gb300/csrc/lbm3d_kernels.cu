@@ -69,6 +69,15 @@ __device__ __forceinline__ int wrap3(int v, int m) {
   return v;
 }
 
+// Periodic wrap of v >= -m into [0, m): a compare and add, and a remainder
+// only on the rare path past one period (halo columns and rows of lattices
+// narrower than a tile).
+__device__ __forceinline__ int wrap_tile(int v, int m) {
+  if (v < 0) v += m;
+  if (v >= m) v %= m;
+  return v;
+}
+
 __device__ __forceinline__ bool map_z(const Inst3& I, int z, int& zm) {
   if ((unsigned)z < (unsigned)I.nz) {
     zm = z;
@@ -212,9 +221,8 @@ __global__ void __launch_bounds__(128) collide3_kernel(const Inst3* __restrict__
     const bool ok = map_z(I, zz, zm);
     for (int idx = tid; idx < (kTY + 2) * (kTX + 2); idx += kTX * kTY) {
       const int lx = idx % (kTX + 2), ly = idx / (kTX + 2);  // constant divisors
-      // the tile's columns and rows lie within one period of the lattice
-      const int gx = wrap3((int)blockIdx.x * kTX + lx - 1, I.nx);
-      const int gy = wrap3((int)blockIdx.y * kTY + ly - 1, I.ny);
+      const int gx = wrap_tile((int)blockIdx.x * kTX + lx - 1, I.nx);
+      const int gy = wrap_tile((int)blockIdx.y * kTY + ly - 1, I.ny);
       tile[slot][ly][lx] = ok ? I.phi[cell3(I, gx, gy, zm)] : 0.0f;
     }
   };
