@@ -342,6 +342,24 @@ void build_items(ij_handle h) {
       h->items.resize(at + n);
       make_items_range(I, k, ch, ya, yb, h->items.data() + at, n);
     }
+  // Items of nozzle-wall strips below the nozzle exit cost more per row
+  // (wetting ghosts, bounce-back): they go first, so that no SM is left
+  // with one of them at the end.
+  const size_t n_body = h->items.size() - [&]() {
+    size_t n = 0;
+    for (int k = 0; k < h->n_inst; k++) {
+      const Inst& I = h->inst[k];
+      n += items_per_range(I, tail_chunk, I.ny - I.ny / 4, I.ny);
+    }
+    return n;
+  }();
+  auto costly = [&](const Item& it) {
+    const Inst& I = h->inst[it.inst];
+    if (I.geom != GEOM_NOZZLE || it.y0 > I.L + 1) return false;
+    const int x0 = it.xs - it.halo, x1 = it.xs + it.nout + it.halo;  // columns held
+    return x1 > I.cx0 - I.wt && x0 < I.cx1 + I.wt;
+  };
+  std::stable_partition(h->items.begin(), h->items.begin() + n_body, costly);
   b.count = (int)h->items.size();
   // one block per item: the block scheduler hands new blocks to SMs as
   // they free up (measured faster than blocks of several items, which hold
