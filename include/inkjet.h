@@ -207,7 +207,10 @@ ij_status ij_kernel_timing(ij_handle h, int enable, double* total_ms, long long*
  * each side) times a chunk of `chunk` rows of one lattice, with the
  * populations staged `prefetch` rows (1..4) ahead of use; every block is
  * one warp (32 threads), so a finished item frees its slot at once.  Every
- * lattice of a handle is in the one bucket of 32-thread blocks.
+ * lattice of a handle is in the one bucket of 32-thread blocks.  The work
+ * list starts with the rows of nozzle-wall strips below the nozzle exit
+ * (costlier per row) and ends with the last eighth of each lattice's rows,
+ * both in chunks a quarter as long, so that the SMs finish together.
  *
  * ij_tune      -- set chunk and prefetch (block_size: 32, or <= 0 for
  *                 every bucket).  Synchronises.

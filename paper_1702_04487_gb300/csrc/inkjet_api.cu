@@ -327,14 +327,14 @@ void build_items(ij_handle h) {
       b.chunk = o.chunk;
       b.prefetch = o.prefetch;
     }
-  // The last quarter of every lattice's rows is cut into chunks a quarter
-  // as long, and those items go last: the final wave of blocks is made of
-  // short items, so SMs run out of work together.
+  // The last eighth of every lattice's rows is cut into chunks a quarter as
+  // long, and those items go last: the final wave of blocks is made of short
+  // items, so SMs run out of work together.
   const int tail_chunk = std::max(4, b.chunk / 4);
   for (int pass = 0; pass < 2; pass++)
     for (int k = 0; k < h->n_inst; k++) {
       const Inst& I = h->inst[k];
-      const int split = I.ny - I.ny / 4;
+      const int split = I.ny - I.ny / 8;
       const int ya = pass == 0 ? 0 : split, yb = pass == 0 ? split : I.ny;
       const int ch = pass == 0 ? b.chunk : tail_chunk;
       const int n = items_per_range(I, ch, ya, yb);
@@ -343,13 +343,13 @@ void build_items(ij_handle h) {
       make_items_range(I, k, ch, ya, yb, h->items.data() + at, n);
     }
   // Items of nozzle-wall strips below the nozzle exit cost more per row
-  // (wetting ghosts, bounce-back): they go first, so that no SM is left
-  // with one of them at the end.
+  // (wetting ghosts, bounce-back): they go first, cut into chunks a quarter
+  // as long, so that no SM is left with a long one of them at the end.
   const size_t n_body = h->items.size() - [&]() {
     size_t n = 0;
     for (int k = 0; k < h->n_inst; k++) {
       const Inst& I = h->inst[k];
-      n += items_per_range(I, tail_chunk, I.ny - I.ny / 4, I.ny);
+      n += items_per_range(I, tail_chunk, I.ny - I.ny / 8, I.ny);
     }
     return n;
   }();
@@ -359,7 +359,23 @@ void build_items(ij_handle h) {
     const int x0 = it.xs - it.halo, x1 = it.xs + it.nout + it.halo;  // columns held
     return x1 > I.cx0 - I.wt && x0 < I.cx1 + I.wt;
   };
-  std::stable_partition(h->items.begin(), h->items.begin() + n_body, costly);
+  const size_t n_costly =
+      std::stable_partition(h->items.begin(), h->items.begin() + n_body, costly) -
+      h->items.begin();
+  if (n_costly > 0) {
+    std::vector<Item> split;
+    for (size_t i = 0; i < n_costly; i++) {
+      const Item& it = h->items[i];
+      for (int y = it.y0; y < it.y0 + it.ch; y += tail_chunk) {
+        Item c = it;
+        c.y0 = y;
+        c.ch = std::min(tail_chunk, it.y0 + it.ch - y);
+        split.push_back(c);
+      }
+    }
+    split.insert(split.end(), h->items.begin() + n_costly, h->items.end());
+    h->items.swap(split);
+  }
   b.count = (int)h->items.size();
   // one block per item: the block scheduler hands new blocks to SMs as
   // they free up (measured faster than blocks of several items, which hold
@@ -998,7 +1014,7 @@ ij_status ij_autotune(ij_handle h, int reps) {
   if (reps < 1) return fail(IJ_ERR_PARAM, "reps must be >= 1");
   if (h->poisoned) return fail(IJ_ERR_STATE, "handle is poisoned");
   if (h->is3d) return IJ_OK;  // the 3-D kernels have one fixed launch shape
-  static const int kChunks[] = {8, 16, 24, 32, 48, 64, 128, 256};
+  static const int kChunks[] = {8, 16, 24, 32, 48, 64, 96, 128, 256};
   cudaEvent_t e0, e1;
   CUDA_TRY(cudaEventCreate(&e0));
   CUDA_TRY(cudaEventCreate(&e1));

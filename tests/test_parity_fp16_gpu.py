@@ -137,9 +137,12 @@ def test_batch_graph_and_tuning_fp16_bitwise(ij):
         fgr, ggr = ij.ij_get_state(hg, k)
         assert np.array_equal(fb, f1) and np.array_equal(gb, g1)
         assert np.array_equal(fb, fgr) and np.array_equal(gb, ggr)
+        # the record's lattice sums add per-item FP64 partial sums, whose
+        # grouping follows the launch shape: equal to FP64 rounding
         ob, _ = ij.ij_observe(hb, k, phi=False)
         og, _ = ij.ij_observe(hg, k, phi=False)
-        assert ob == og
+        assert ob.keys() == og.keys()
+        assert all(abs(ob[key] - og[key]) <= 1e-12 * max(1.0, abs(ob[key])) for key in ob)
 
 
 def test_set_get_state_round_trip(ij):
