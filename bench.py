@@ -30,18 +30,24 @@ BYTES_PER_LUP = {"2d": 112, "2d16": 60, "3d32": 208, "3d16": 108}
 FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes per step-kernel launch from an ncu capture (dram__bytes_read.sum
 # + dram__bytes_write.sum, mean of two launches without diagnostics) of the
-# workload, valid only for the kernel source whose sha256 prefix and the row
-# chunk are recorded with it.
+# workload, valid only for the sources (kernel_hash) and the row chunk
+# recorded with it.
 NCU_TRAFFIC = {
-    "cfg2": {"kernel_sha": "1fdcbd5973e35985", "chunk": 24, "bytes_per_step": 749.33e6},
-    "cfg2h": {"kernel_sha": "1fdcbd5973e35985", "chunk": 24, "bytes_per_step": 369.84e6},
+    "cfg2": {"kernel_sha": "3f360a8e388af1d3", "chunk": 64, "bytes_per_step": 743.98e6},
+    "cfg2h": {"kernel_sha": "3f360a8e388af1d3", "chunk": 64, "bytes_per_step": 392.14e6},
 }
 
 
 def kernel_hash(params):
-    name = "lbm3d_kernels.cu" if params[0].get("dim", 2) == 3 else "lbm2d_kernels.cu"
-    with open(os.path.join(ROOT, "paper_1702_04487_gb300", "csrc", name), "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()[:16]
+    """sha256 prefix of the sources that fix the step kernel's DRAM traffic:
+    the kernels, and for 2-D the host code that builds the work list."""
+    names = (["lbm3d_kernels.cu"] if params[0].get("dim", 2) == 3
+             else ["lbm2d_kernels.cu", "inkjet_api.cu"])
+    h = hashlib.sha256()
+    for name in names:
+        with open(os.path.join(ROOT, "paper_1702_04487_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def lattice_kind(p):
