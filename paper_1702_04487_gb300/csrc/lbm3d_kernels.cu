@@ -191,11 +191,11 @@ constexpr int kZChunk = 8;
 constexpr int kTX = 32, kTY = 4;
 
 template <bool H, bool DIAG>
-__global__ void __launch_bounds__(128) collide3_kernel(const Inst3* __restrict__ insts, int index,
+__global__ void __launch_bounds__(kTX * kTY) collide3_kernel(const Inst3* __restrict__ insts, int index,
                                                        const long long* __restrict__ d_t,
                                                        int t_off) {
   __shared__ float tile[4][kTY + 2][kTX + 2];
-  __shared__ float red[4][6];
+  __shared__ float red[kTY][6];
   const Inst3& I = insts[index];
   // a lattice whose numeric flag is set is frozen; one read per block keeps
   // the decision uniform over the block's barriers below
@@ -340,7 +340,7 @@ __global__ void __launch_bounds__(128) collide3_kernel(const Inst3* __restrict__
       __syncthreads();
       if (tid == 0) {
         double s[6] = {0, 0, 0, 0, 0, 0};
-        for (int wq = 0; wq < 4; wq++)
+        for (int wq = 0; wq < kTY; wq++)
           for (int k = 0; k < 6; k++) s[k] += (double)red[wq][k];
         atomicAdd(I.rows + z, s[0]);
         atomicAdd(I.rows + I.nz + z, s[1]);
@@ -577,7 +577,7 @@ cudaError_t launch_init3(const Inst3* d, const Inst3& h, int index, cudaStream_t
 
 cudaError_t launch_collide3(const Inst3* d, const Inst3& h, int index, const long long* d_t,
                             int t_off, bool diag, cudaStream_t s) {
-  const dim3 g = grid3c(h), b(32, 4);
+  const dim3 g = grid3c(h), b(kTX, kTY);
   if (h.fp16) {
     if (diag)
       collide3_kernel<true, true><<<g, b, 0, s>>>(d, index, d_t, t_off);
