@@ -55,7 +55,8 @@ typedef enum {
   IJ_ERR_PARAM = 1,   /* invalid argument; nothing was changed */
   IJ_ERR_CUDA = 2,    /* a CUDA call failed; see ij_last_error */
   IJ_ERR_NUMERIC = 3, /* NaN or |u| > 0.3 met in a step of a lattice */
-  IJ_ERR_TIMEOUT = 4, /* reserved: no kernel of this library spins */
+  IJ_ERR_TIMEOUT = 4, /* a bounded wait inside a kernel ran out (the surrogate's
+                         tensor-core pipeline); the LBM step kernels never wait */
   IJ_ERR_STATE = 5,   /* call not allowed in the handle's state */
   IJ_ERR_OOM = 6      /* the allocator returned NULL */
 } ij_status;
