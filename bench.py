@@ -75,6 +75,7 @@ def device_bytes(p):
 
 
 def workload(name, rank=0):
+    import numpy as np
     from paper_1702_04487_gb300 import workloads as W
     if name in ("cfg2", "cfg2h"):
         ps = W.cfg2_sweep(seed=2 + rank)
@@ -82,6 +83,10 @@ def workload(name, rank=0):
         if name == "cfg2h":
             ps = [dict(p, precision=1) for p in ps]
             desc = desc.replace("FP32", "FP16 offset storage")
+    elif name == "e1":
+        ps = [W.e1(F0=f) for f in np.geomspace(2e-3, 3e-2, 16)]
+        desc = ("the paper's lattice: 200x800, density ratio 1000, 16 drive amplitudes F0 in "
+                "[2e-3, 3e-2], FP32")
     elif name == "big":
         ps = [W.big_nozzle()]
         desc = "2048x8192 nozzle (200x1600 geometry scaled), 1 lattice, FP32"
@@ -503,7 +508,7 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=("native", "reference"), default="native")
-    ap.add_argument("--workload", choices=("cfg2", "cfg2h", "big", "cfg3", "cfg4", "cfg4h"),
+    ap.add_argument("--workload", choices=("cfg2", "cfg2h", "big", "cfg3", "cfg4", "cfg4h", "e1"),
                     default="cfg2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",

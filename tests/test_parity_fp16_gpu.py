@@ -145,6 +145,14 @@ def test_batch_graph_and_tuning_fp16_bitwise(ij):
         assert all(abs(ob[key] - og[key]) <= 1e-12 * max(1.0, abs(ob[key])) for key in ob)
 
 
+def test_mixed_precision_batch_is_rejected(ij):
+    """One launch covers every lattice of a handle, so they share the
+    storage format."""
+    with pytest.raises(ij.InkjetError) as e:
+        ij.ij_create([dict(W.small_nozzle(), precision=1), W.small_nozzle()])
+    assert e.value.status == ij.IJ_ERR_PARAM
+
+
 def test_set_get_state_round_trip(ij):
     """get_state returns absolute FP32 populations and set_state rounds them
     to FP16 offsets again: g comes back exactly (g_0 is FP32, g_1..4 decode

@@ -68,6 +68,19 @@ def test_noalloc_step_matches_handle_step_twice():
                 assert abs(r[col] - obs[key]) <= 1e-6 * max(1.0, abs(obs[key]))
 
 
+def test_noalloc_rejects_fp16_storage():
+    """The allocation-free step takes FP32 buffers only; FP16 storage is
+    refused on the host before any device work."""
+    from paper_1702_04487_gb300 import inkjet, workloads as W
+
+    p = inkjet.make_params(W.small_nozzle(precision=1))
+    dummy = C.c_void_p(16)
+    st = inkjet._lib.ij_step_noalloc(C.byref(p), 0, dummy, dummy, C.c_void_p(32),
+                                     C.c_void_p(48), None, None)
+    assert st == inkjet.IJ_ERR_PARAM
+    assert "FP32" in inkjet.ij_last_error()
+
+
 def test_noalloc_rejects_lattices_beyond_its_fixed_scratch():
     from paper_1702_04487_gb300 import inkjet, workloads as W
 
