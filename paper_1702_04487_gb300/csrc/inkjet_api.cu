@@ -357,7 +357,8 @@ void build_items(ij_handle h) {
     const Inst& I = h->inst[it.inst];
     if (I.geom != GEOM_NOZZLE || it.y0 > I.L + 1) return false;
     const int x0 = it.xs - it.halo, x1 = it.xs + it.nout + it.halo;  // columns held
-    return x1 > I.cx0 - I.wt && x0 < I.cx1 + I.wt;
+    // either wall band [cx0 - wt, cx0) or [cx1, cx1 + wt) among them
+    return (x1 > I.cx0 - I.wt && x0 < I.cx0) || (x1 > I.cx1 && x0 < I.cx1 + I.wt);
   };
   const size_t n_costly =
       std::stable_partition(h->items.begin(), h->items.begin() + n_body, costly) -
