@@ -317,16 +317,17 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kStepBlocksPerSM)
     __half* __restrict__ ghout = reinterpret_cast<__half*>(gout + N);
     const bool any_edge = H && __any_sync(kFull, edge);
 
-    // Stage pipeline row r into ring slot sp (own column; f only for rows
-    // that are collided), as one cp.async group.
+    // Stage pipeline row r into ring slot sp (the lane's own column, or in
+    // FP16 storage the pair of columns of an even lane; f only for rows that
+    // are collided), as one cp.async group.
     auto stage = [&](int r, int sp) {
       int ym;
       if (r <= y0 + ch + 2 && map_row_v(r, ny, bc, ym)) {  // uniform over the warp
         const unsigned d = ring_sa + sp * (kRowW * 4);
         const bool own = row_kind(geom, ck, L, wt, ym) == 0;
         const bool frow = r >= y0 - 1 && r <= y0 + ch;
-        // a solid edge lane has no populations of its own: the g of the
-        // column outside the strip go where its f would be
+        // a solid edge lane with a fluid cell beyond the strip stages that
+        // cell's g (FP32: where its own f would be; FP16: slots of its own)
         const bool outer = edge && !own && row_kind(geom, cko, L, wt, ym) == 0;
         if (!H) {
           const bool fneed = own && col_lane && frow;
