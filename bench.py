@@ -30,11 +30,13 @@ BYTES_PER_LUP = {"2d": 112, "2d16": 60, "3d32": 208, "3d16": 108}
 FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes per step-kernel launch from an ncu capture (dram__bytes_read.sum
 # + dram__bytes_write.sum, mean of two launches without diagnostics) of the
-# workload, valid only for the sources (kernel_hash) and the row chunk
-# recorded with it.
+# workload, by row chunk, valid only for the sources (kernel_hash) recorded
+# with them.
 NCU_TRAFFIC = {
-    "cfg2": {"kernel_sha": "3f360a8e388af1d3", "chunk": 64, "bytes_per_step": 743.98e6},
-    "cfg2h": {"kernel_sha": "3f360a8e388af1d3", "chunk": 64, "bytes_per_step": 392.14e6},
+    "cfg2": {"kernel_sha": "82604d2c93b18130",
+             "bytes_per_step": {48: 748.68e6, 64: 748.53e6, 96: 747.34e6, 128: 735.47e6}},
+    "cfg2h": {"kernel_sha": "82604d2c93b18130",
+              "bytes_per_step": {48: 392.77e6, 64: 391.57e6, 96: 390.69e6, 128: 388.58e6}},
 }
 
 
@@ -327,9 +329,9 @@ def run_native(args):
         achieved = bpl * cells / (per_step_ms / 1e3) / 1e9
         traffic = None
         rec = NCU_TRAFFIC.get(args.workload)
-        if (rec and rec.get("kernel_sha") == kernel_hash(params)
-                and all(b["chunk"] == rec["chunk"] for b in tuning)):
-            traffic = rec["bytes_per_step"]
+        chunks = {b["chunk"] for b in tuning}
+        if rec and rec.get("kernel_sha") == kernel_hash(params) and len(chunks) == 1:
+            traffic = rec["bytes_per_step"].get(chunks.pop())
         line = {
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
