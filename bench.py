@@ -199,6 +199,7 @@ def oracle_sample(params):
         q = {k: v for k, v in q.items() if k not in ("dim", "precision")}
         return OracleSim3(q), q, "%dx%dx%d downscale of lattice 0" % (q["nx"], q["ny"], q["nz"])
     from oracle import OracleSim
+    p = {k: v for k, v in p.items() if k != "precision"}  # the oracle is FP64 only
     return OracleSim(p), p, "one %dx%d lattice (lattice 0 of the workload)" % (p["nx"], p["ny"])
 
 
