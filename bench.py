@@ -52,6 +52,16 @@ def kernel_hash(params):
     return h.hexdigest()[:16]
 
 
+def recorded_traffic(name, params, tuning):
+    """The recorded DRAM bytes per step-kernel launch of this workload at the
+    launch shape in use, or None (no record, other sources, other chunk)."""
+    rec = NCU_TRAFFIC.get(name)
+    chunks = {b["chunk"] for b in tuning}
+    if not rec or rec.get("kernel_sha") != kernel_hash(params) or len(chunks) != 1:
+        return None
+    return rec["bytes_per_step"].get(chunks.pop())
+
+
 def lattice_kind(p):
     h = p.get("precision", 0) == 1
     if p.get("dim", 2) != 3:
@@ -328,11 +338,7 @@ def run_native(args):
         per_step_ms = k_ms / k_steps
         bpl = BYTES_PER_LUP[kind]
         achieved = bpl * cells / (per_step_ms / 1e3) / 1e9
-        traffic = None
-        rec = NCU_TRAFFIC.get(args.workload)
-        chunks = {b["chunk"] for b in tuning}
-        if rec and rec.get("kernel_sha") == kernel_hash(params) and len(chunks) == 1:
-            traffic = rec["bytes_per_step"].get(chunks.pop())
+        traffic = recorded_traffic(args.workload, params, tuning)
         line = {
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
