@@ -331,7 +331,9 @@ void build_items(ij_handle h) {
   // long, and those items go last: the final wave of blocks is made of short
   // items, so SMs run out of work together.
   const int tail_chunk = std::max(4, b.chunk / 4);
-  for (int pass = 0; pass < 2; pass++)
+  size_t n_body = 0;  // items before the tail
+  for (int pass = 0; pass < 2; pass++) {
+    if (pass == 1) n_body = h->items.size();
     for (int k = 0; k < h->n_inst; k++) {
       const Inst& I = h->inst[k];
       const int split = I.ny - I.ny / 8;
@@ -342,17 +344,10 @@ void build_items(ij_handle h) {
       h->items.resize(at + n);
       make_items_range(I, k, ch, ya, yb, h->items.data() + at, n);
     }
+  }
   // Items of nozzle-wall strips below the nozzle exit cost more per row
   // (wetting ghosts, bounce-back): they go first, cut into chunks a quarter
   // as long, so that no SM is left with a long one of them at the end.
-  const size_t n_body = h->items.size() - [&]() {
-    size_t n = 0;
-    for (int k = 0; k < h->n_inst; k++) {
-      const Inst& I = h->inst[k];
-      n += items_per_range(I, tail_chunk, I.ny - I.ny / 8, I.ny);
-    }
-    return n;
-  }();
   auto costly = [&](const Item& it) {
     const Inst& I = h->inst[it.inst];
     if (I.geom != GEOM_NOZZLE || it.y0 > I.L + 1) return false;
