@@ -4,7 +4,9 @@
  * to D3Q19/D3Q7) with a round nozzle.
  *
  * TEST INFRASTRUCTURE ONLY (see lbm_oracle.h): plain whole-field loops in the
- * order of the method, no tiling or fusion, shared with nothing else.
+ * order of the method, no tiling or fusion, shared with nothing else.  Passes
+ * whose cells are independent may run their planes on several OpenMP
+ * threads, with bit-identical results on any number of threads.
  *
  * The paper is 2-D.  The 3-D lattice keeps the same readings as the 2-D
  * oracle (Guo half-force velocity, rest direction special in the g
@@ -58,13 +60,20 @@ typedef struct {
   double m_prev, t_prev, breakup;
 } orc3;
 
+/* Weights and opposite directions of the table above, filled on first use
+ * (always from one thread: orc3_create, or a direct call of the per-cell
+ * functions) and read only afterwards. */
+static int tables_ready = 0;
+
 static void init_tables(void) {
+  if (tables_ready) return;
   for (int i = 0; i < 19; i++) {
     int a = EX[i] * EX[i] + EY[i] * EY[i] + EZ[i] * EZ[i];
     WT[i] = a == 0 ? 1.0 / 3.0 : (a == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
     for (int j = 0; j < 19; j++)
       if (EX[j] == -EX[i] && EY[j] == -EY[i] && EZ[j] == -EZ[i]) OPP[i] = j;
   }
+  tables_ready = 1;
 }
 
 static int wrap(int v, int m) {
@@ -201,6 +210,7 @@ static double* phih_ptr(orc3* s, int x, int y, int z) {
 }
 
 static void fill_phih(orc3* s) {
+#pragma omp parallel for schedule(static)
   for (int z = -2; z < s->nz + 2; z++)
     for (int y = 0; y < s->ny; y++)
       for (int x = 0; x < s->nx; x++)
@@ -241,6 +251,7 @@ double orc3_uniform(unsigned long long seed, int x, int y, int z) { return unifo
 static void chem_and_velocity(orc3* s, long long t) {
   int nx = s->nx, ny = s->ny, nz = s->nz;
   double Fd = drive_at(&s->p, t);
+#pragma omp parallel for schedule(static)
   for (int z = -1; z <= nz; z++) {
     int zm;
     if (!map_z(s, z, &zm)) continue;
@@ -365,6 +376,7 @@ static void diagnose(orc3* s, long long t) {
 
 static void moments(orc3* s) {
   size_t N = (size_t)s->nx * s->ny * s->nz;
+#pragma omp parallel for schedule(static)
   for (size_t c = 0; c < N; c++) {
     if (s->kind[c] != 0) continue;
     double n = 0, m[3] = {0, 0, 0}, phi = 0;
@@ -388,6 +400,7 @@ static void collide(orc3* s) {
   int nx = s->nx, ny = s->ny, nz = s->nz;
   size_t N = (size_t)nx * ny * nz, NM = (size_t)nx * ny * (nz + 2);
   const orc_params* p = &s->p;
+#pragma omp parallel for schedule(static)
   for (int z = -1; z <= nz; z++) {
     int zm;
     if (!map_z(s, z, &zm)) continue;
@@ -423,6 +436,7 @@ static void collide(orc3* s) {
 static void stream(orc3* s) {
   int nx = s->nx, ny = s->ny, nz = s->nz;
   size_t N = (size_t)nx * ny * nz, NM = (size_t)nx * ny * (nz + 2);
+#pragma omp parallel for schedule(static)
   for (int z = 0; z < nz; z++)
     for (int y = 0; y < ny; y++)
       for (int x = 0; x < nx; x++) {

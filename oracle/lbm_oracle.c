@@ -4,7 +4,10 @@
  * whole-field loops in the order the paper states the method.
  *
  * TEST INFRASTRUCTURE ONLY: see lbm_oracle.h.  Nothing here is tiled, fused
- * or reordered; each pass below is one step of the method.
+ * or reordered; each pass below is one step of the method.  Passes whose
+ * cells are independent (each iteration writes only its own cell) may run
+ * their rows on several OpenMP threads; the arithmetic of every cell is the
+ * same on any number of threads, so results are bit-identical.
  *
  * Readings of what the paper leaves open (each is listed, with its reason,
  * in the design notes of the repository):
@@ -31,6 +34,9 @@
 #include "lbm_oracle.h"
 
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -238,6 +244,7 @@ static double ghost_value(const orc_sim* s, const double* phi, int x, int y) {
  * extended rows -2..ny+1. */
 static void fill_phih(orc_sim* s, const double* phi) {
   int nx = s->nx, ny = s->ny;
+#pragma omp parallel for schedule(static)
   for (int y = -2; y < ny + 2; y++)
     for (int x = 0; x < nx; x++)
       s->phih[(size_t)(y + 2) * nx + x] =
@@ -253,6 +260,7 @@ static double phih_at(const orc_sim* s, int x, int y) {
  * phi(x+c_i); mu = 4 A phi (phi^2 - phi*^2) - kappa lap. */
 static void chem_potential(orc_sim* s) {
   int nx = s->nx, ny = s->ny;
+#pragma omp parallel for schedule(static)
   for (int y = -1; y <= ny; y++)
     for (int x = 0; x < nx; x++) {
       size_t c = (size_t)(y + 1) * nx + x;
@@ -412,6 +420,7 @@ void orc_set_state(orc_sim* s, const double* f, const double* g, long long t) {
 /* Pass 1 (Eq. 3, 8 definitions): n = sum f_i, phi = sum g_i, momentum. */
 static void moments(orc_sim* s) {
   size_t N = (size_t)s->nx * s->ny;
+#pragma omp parallel for schedule(static)
   for (size_t c = 0; c < N; c++) {
     if (s->kind[c] != 0) continue;
     double n = 0, mx = 0, my = 0, phi = 0;
@@ -434,6 +443,7 @@ static void moments(orc_sim* s) {
 static void velocity(orc_sim* s, long long t) {
   int nx = s->nx, ny = s->ny;
   double Fd = drive_at(&s->p, t);
+#pragma omp parallel for schedule(static)
   for (int y = -1; y <= ny; y++) {
     int ym;
     if (!map_y(s, y, &ym)) continue;
@@ -458,6 +468,7 @@ static void collide(orc_sim* s) {
   int nx = s->nx, ny = s->ny;
   size_t N = (size_t)nx * ny, NM = (size_t)nx * (ny + 2);
   const orc_params* p = &s->p;
+#pragma omp parallel for schedule(static)
   for (int y = -1; y <= ny; y++) {
     int ym;
     if (!map_y(s, y, &ym)) continue;
@@ -498,6 +509,7 @@ static void collide(orc_sim* s) {
 static void stream(orc_sim* s) {
   int nx = s->nx, ny = s->ny;
   size_t N = (size_t)nx * ny, NM = (size_t)nx * (ny + 2);
+#pragma omp parallel for schedule(static)
   for (int y = 0; y < ny; y++)
     for (int x = 0; x < nx; x++) {
       size_t c = (size_t)y * nx + x, cm = (size_t)(y + 1) * nx + x;
@@ -716,4 +728,21 @@ void orc_fields(orc_sim* s, double* n, double* phi, double* mu, double* ux, doub
     if (ux) ux[c] = fl ? s->ux[e] : 0.0;
     if (uy) uy[c] = fl ? s->uy[e] : 0.0;
   }
+}
+
+/* Threads of the per-cell passes (1 without OpenMP). */
+int orc_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
 }

@@ -103,6 +103,10 @@ void orc_geq(double phi, double mu, double ux, double uy, double gamma, double q
 void orc_force_term(double tau, double ux, double uy, double Fx, double Fy, double* F9);
 double orc_omega_of_theta(double theta_deg);
 double orc_uniform(unsigned long long seed, int x, int y);
+/* Threads of the per-cell passes (OpenMP; 1 when built without it).  Every
+ * result is bit-identical on any number of threads. */
+int orc_threads(void);
+void orc_set_threads(int n);
 
 #ifdef __cplusplus
 }

@@ -71,6 +71,9 @@ def _load():
         lib.orc_omega_of_theta.argtypes = [C.c_double]
         lib.orc_uniform.restype = C.c_double
         lib.orc_uniform.argtypes = [C.c_ulonglong, C.c_int, C.c_int]
+        lib.orc_threads.restype = C.c_int
+        lib.orc_threads.argtypes = []
+        lib.orc_set_threads.argtypes = [C.c_int]
         _lib = lib
     return _lib
 
@@ -179,6 +182,16 @@ def omega_of_theta(theta_deg):
 
 def uniform(seed, x, y):
     return _load().orc_uniform(seed, x, y)
+
+
+def threads():
+    """Threads the oracle's per-cell passes run on (1 without OpenMP)."""
+    return _load().orc_threads()
+
+
+def set_threads(n):
+    """Run the per-cell passes on n threads (results are bit-identical)."""
+    _load().orc_set_threads(int(n))
 
 
 def _load3():
