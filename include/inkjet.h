@@ -236,13 +236,12 @@ ij_status ij_get_tuning(ij_handle h, int bucket, int* block_size, int* chunk, in
 
 /*
  * ij_step_noalloc -- one time step of ONE lattice between device buffers the
- * caller owns, allocating nothing (no device memory, no host heap).  The
- * paper has no counterpart: this is a service for callers that may not
- * allocate where they step the lattice -- a plugin inside another framework
- * that owns all device memory through its own pool, a loop that must keep a
- * fixed memory footprint, or code running while its stream is recorded, where
- * cudaMalloc is not allowed.  It computes exactly what ij_step computes for a
- * one-lattice handle.
+ * caller owns, allocating no device memory.  The paper has no counterpart:
+ * this is a service for callers that may not allocate where they step the
+ * lattice -- a plugin inside another framework that owns all device memory
+ * through its own pool, or a loop that must keep a fixed memory footprint
+ * (allocator calls have a latency and a fragmentation it cannot bound).  It
+ * computes exactly what ij_step computes for a one-lattice handle.
  *   params        : the lattice (host memory); nx, ny, geometry as in ij_create;
  *                   2-D FP32 storage only (dim 3 or IJ_FP16_STORE returns
  *                   IJ_ERR_PARAM).
@@ -257,7 +256,13 @@ ij_status ij_get_tuning(ij_handle h, int bucket, int* block_size, int* chunk, in
  *                   diagnostics record of the state at t, or NULL for none.
  *                   Each call starts a fresh breakup history, so breakup_step
  *                   is t when the neck is already closed, else -1.
- *   stream        : cudaStream_t to enqueue on; the call is asynchronous.
+ *   status_out    : device, one unsigned receiving the step's numeric flag, or
+ *                   NULL.  Nonzero means the step met NaN or |u| > 0.3: the
+ *                   kernel then stops writing, so f_out and g_out are only
+ *                   partly written and must be discarded.
+ *   stream        : cudaStream_t to enqueue on (NULL: the legacy default
+ *                   stream); it must belong to the current device, else
+ *                   IJ_ERR_PARAM.  The call is asynchronous.
  * Limits: ny <= 8192 and at most 16384 work items (strips of 28 columns times
  * chunks of 64 rows); larger lattices are rejected with IJ_ERR_PARAM.
  * Descriptors and scratch live in one fixed device array of about 0.6 MB per
@@ -265,12 +270,13 @@ ij_status ij_get_tuning(ij_handle h, int bucket, int* block_size, int* chunk, in
  * on a device looks up that array's device address, so make it before any
  * stream capture.  Every call shares the array: calls whose GPU work
  * overlaps (for example on two streams) race, so order them on one stream.
- * The numeric flag is cleared at each call and not reported; NaN shows in the
- * record.  Errors: IJ_ERR_PARAM, IJ_ERR_CUDA.
+ * The descriptor, the time and the work list are copied from static host
+ * buffers with cudaMemcpyAsync under a mutex (no host heap either).
+ * Errors: IJ_ERR_PARAM, IJ_ERR_CUDA.
  */
 ij_status ij_step_noalloc(const ij_params* params, long long t, const float* f_in,
                           const float* g_in, float* f_out, float* g_out, double* record_out,
-                          void* stream);
+                          unsigned* status_out, void* stream);
 
 /* ij_destroy -- synchronise and release everything (NULL is accepted). */
 ij_status ij_destroy(ij_handle h);

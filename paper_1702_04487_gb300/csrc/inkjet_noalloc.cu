@@ -1,15 +1,14 @@
 // ij_step_noalloc: one time step of one lattice between caller-owned device
-// buffers, with no device or host heap allocation.
+// buffers, with no device allocation.
 //
 // Who needs it: a caller that may not allocate device memory at the point
 // where it steps the lattice -- for example a plugin living inside another
-// framework that owns every byte of the device through its own pool, a
+// framework that owns every byte of the device through its own pool, or a
 // solver loop that must keep a fixed memory footprint (no allocator calls,
-// whose latency and fragmentation it cannot bound), or code that runs while
-// its stream is being recorded and so may not call cudaMalloc.  ij_create
-// would allocate the lattice, its descriptors and its diagnostics scratch;
-// this entry point takes the populations from the caller and keeps
-// everything else in a fixed file-scope device array.
+// whose latency and fragmentation it cannot bound).  ij_create would
+// allocate the lattice, its descriptors and its diagnostics scratch; this
+// entry point takes the populations from the caller and keeps everything
+// else in a fixed file-scope device array.
 //
 // The array below is sized for one lattice of at most kMaxRows rows and
 // kMaxItems work items; every GPU that loads the library holds it (about
@@ -17,6 +16,11 @@
 // keeps the last call's contents, so each call clears the parts that must
 // start at zero, and calls whose GPU work overlaps (for example on two
 // streams) race on it.
+//
+// Host side: the descriptor and the work list are built in static host
+// buffers under one mutex and handed to cudaMemcpyAsync, which has consumed
+// a pageable source by the time it returns; so no host heap is touched
+// either, and concurrent host threads serialise on the mutex.
 #include <cuda_runtime.h>
 #include <string.h>
 
@@ -48,18 +52,28 @@ constexpr size_t kScratchBytes = kOffHist + a256(kRec * sizeof(double));
 // Descriptor, work list, time, numeric flag and FP64 diagnostics scratch.
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-std::mutex g_mu;
+std::mutex g_mu;                          // guards g_base and the staging below
 unsigned char* g_base[kMaxDevices] = {};  // device address of g_scratch per device
-thread_local Item t_items[kMaxItems];     // staging of the work list (no heap)
+Item g_items[kMaxItems];                  // host staging of the work list (static, no heap)
 
 // Device address of g_scratch on the current device, looked up once per
-// device (the host-side name of the array is not a device address).
-ij_status scratch_base(unsigned char** out) {
+// device (the host-side name of the array is not a device address).  The
+// caller holds g_mu.  A stream that belongs to another device is refused:
+// its kernels would run there against this device's scratch address.
+ij_status scratch_base(cudaStream_t stream, unsigned char** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return report(IJ_ERR_CUDA, cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return report(IJ_ERR_CUDA, "device ordinal out of range");
-  std::lock_guard<std::mutex> lock(g_mu);
+  if (stream) {
+    int sdev = -1;
+    e = cudaStreamGetDevice(stream, &sdev);
+    if (e != cudaSuccess) return report(IJ_ERR_CUDA, cudaGetErrorString(e));
+    if (sdev != dev)
+      return report(IJ_ERR_PARAM,
+                    "ij_step_noalloc: the stream belongs to another device; make that device "
+                    "current first");
+  }
   if (!g_base[dev]) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_scratch);
@@ -76,7 +90,7 @@ ij_status scratch_base(unsigned char** out) {
 
 extern "C" ij_status ij_step_noalloc(const ij_params* params, long long t, const float* f_in,
                                      const float* g_in, float* f_out, float* g_out,
-                                     double* record_out, void* stream) {
+                                     double* record_out, unsigned* status_out, void* stream) {
   if (!params || !f_in || !g_in || !f_out || !g_out)
     return report(IJ_ERR_PARAM, "ij_step_noalloc: params and the four population buffers are required");
   if (t < 0) return report(IJ_ERR_PARAM, "ij_step_noalloc: t < 0");
@@ -90,13 +104,15 @@ extern "C" ij_status ij_step_noalloc(const ij_params* params, long long t, const
     return report(IJ_ERR_PARAM, "ij_step_noalloc: FP32 storage only");
   if (p.ny > kMaxRows)
     return report(IJ_ERR_PARAM, "ij_step_noalloc: ny exceeds the fixed scratch limit of 8192 rows");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> lock(g_mu);
   // work list: the same strips and row chunks ij_create builds for one lattice
   Inst I = derive_params(p);
-  const int n_items = make_items(I, 0, kChunk, t_items, kMaxItems);
+  const int n_items = make_items(I, 0, kChunk, g_items, kMaxItems);
   if (n_items < 0)
     return report(IJ_ERR_PARAM, "ij_step_noalloc: lattice needs more than the fixed 16384 work items");
   unsigned char* base = nullptr;
-  st = scratch_base(&base);
+  st = scratch_base(s, &base);
   if (st != IJ_OK) return st;
 
   I.f[t & 1] = const_cast<float*>(f_in);
@@ -112,7 +128,6 @@ extern "C" ij_status ij_step_noalloc(const ij_params* params, long long t, const
   const Item* d_items = reinterpret_cast<const Item*>(base + kOffItems);
   long long* d_t = reinterpret_cast<long long*>(base + kOffT);
   const double dinit[8] = {0, 0, 0, -1, 0, 0, 0, 0};
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   const bool diag = record_out != nullptr;
 #define NOALLOC_TRY(expr)                                              \
   do {                                                                 \
@@ -120,7 +135,7 @@ extern "C" ij_status ij_step_noalloc(const ij_params* params, long long t, const
     if (e_ != cudaSuccess) return report(IJ_ERR_CUDA, cudaGetErrorString(e_)); \
   } while (0)
   NOALLOC_TRY(cudaMemcpyAsync(base + kOffInst, &I, sizeof(Inst), cudaMemcpyHostToDevice, s));
-  NOALLOC_TRY(cudaMemcpyAsync(base + kOffItems, t_items, (size_t)n_items * sizeof(Item),
+  NOALLOC_TRY(cudaMemcpyAsync(base + kOffItems, g_items, (size_t)n_items * sizeof(Item),
                               cudaMemcpyHostToDevice, s));
   NOALLOC_TRY(cudaMemcpyAsync(d_t, &t, sizeof(long long), cudaMemcpyHostToDevice, s));
   // what must start at zero: the numeric flag, and for a record the row and
@@ -139,6 +154,11 @@ extern "C" ij_status ij_step_noalloc(const ij_params* params, long long t, const
     NOALLOC_TRY(cudaMemcpyAsync(record_out, base + kOffHist, kRec * sizeof(double),
                                 cudaMemcpyDeviceToDevice, s));
   }
+  // the step kernel stops writing a lattice once its flag is set, so the
+  // caller must learn of it to discard a partly written output
+  if (status_out)
+    NOALLOC_TRY(cudaMemcpyAsync(status_out, base + kOffStatus, sizeof(unsigned),
+                                cudaMemcpyDeviceToDevice, s));
 #undef NOALLOC_TRY
   return IJ_OK;
 }

@@ -79,7 +79,7 @@ _sig = {
     "ij_time": [_vp, C.POINTER(_ll)],
     "ij_launch_count": [_vp, C.POINTER(_ll)],
     "ij_kernel_timing": [_vp, _i, _dp, C.POINTER(_ll)],
-    "ij_step_noalloc": [C.POINTER(ij_params), _ll, _fp, _fp, _fp, _fp, _fp, _vp],
+    "ij_step_noalloc": [C.POINTER(ij_params), _ll, _fp, _fp, _fp, _fp, _fp, _fp, _vp],
     "ij_tune": [_vp, _i, _i, _i],
     "ij_autotune": [_vp, _i],
     "ij_use_graph": [_vp, _i],
