@@ -204,9 +204,9 @@ ij_status ij_kernel_timing(ij_handle h, int enable, double* total_ms, long long*
 
 /*
  * Launch-shape tuning (no counterpart in the paper).  The step kernel runs
- * one warp per work item: a strip of 28 columns (plus two halo columns on
- * each side) times a chunk of `chunk` rows of one lattice, with the
- * populations staged `prefetch` rows (1..4) ahead of use; every block is
+ * one warp per work item: a strip of 60 columns, two per lane (plus two halo
+ * columns on each side), times a chunk of `chunk` rows of one lattice, with
+ * the populations staged `prefetch` rows (1..4) ahead of use; every block is
  * one warp (32 threads), so a finished item frees its slot at once.  Every
  * lattice of a handle is in the one bucket of 32-thread blocks.  The work
  * list starts with the rows of nozzle-wall strips below the nozzle exit
@@ -263,7 +263,7 @@ ij_status ij_get_tuning(ij_handle h, int bucket, int* block_size, int* chunk, in
  *   stream        : cudaStream_t to enqueue on (NULL: the legacy default
  *                   stream); it must belong to the current device, else
  *                   IJ_ERR_PARAM.  The call is asynchronous.
- * Limits: ny <= 8192 and at most 16384 work items (strips of 28 columns times
+ * Limits: ny <= 8192 and at most 16384 work items (strips of 60 columns times
  * chunks of 64 rows); larger lattices are rejected with IJ_ERR_PARAM.
  * Descriptors and scratch live in one fixed device array of about 0.6 MB per
  * GPU that loads the library, kept until the process exits.  The first call

@@ -71,6 +71,7 @@ struct ij_handle_s {
   // record kernel and the observation calls
   bool is3d = false;
   bool fp16 = false;  // 2-D lattices in FP16 storage
+  bool odd = false;   // some 2-D lattice has an odd nx (column-by-column copies)
   std::vector<Inst3> inst3;
   Inst3* d_inst3 = nullptr;
   float* stage = nullptr;  // FP32 staging of exported / imported states (3-D, 2-D FP16)
@@ -458,7 +459,7 @@ ij_status one_step(ij_handle h) {
       CUDA_TRY(cudaEventRecord(e0, h->stream));
     }
     CUDA_TRY(launch_step(h->d_inst, h->d_items + b.first, b.count, b.nthreads, b.grid, h->d_t, 0,
-                         diag, b.prefetch, h->fp16, h->stream));
+                         diag, b.prefetch, h->fp16, h->odd, h->stream));
     h->launches++;
     if (h->timing) {
       CUDA_TRY(cudaEventRecord(e1, h->stream));
@@ -495,7 +496,7 @@ ij_status build_graph(ij_handle h) {
     }
     for (const Bucket& b : h->buckets) {
       e = launch_step(h->d_inst, h->d_items + b.first, b.count, b.nthreads, b.grid, h->d_t, j,
-                      diag, b.prefetch, h->fp16, cs);
+                      diag, b.prefetch, h->fp16, h->odd, cs);
       n++;
       if (e != cudaSuccess) break;
     }
@@ -728,6 +729,8 @@ ij_status ij_create(const ij_params* params, int count, ij_alloc_fn alloc, ij_fr
     if (params[k].precision != params[0].precision)
       return bail(fail(IJ_ERR_PARAM, "all 2-D lattices of a batch must share the precision"));
   h->fp16 = params[0].precision == IJ_FP16_STORE;
+  for (int k = 0; k < count; k++)
+    if (params[k].nx % 2 != 0) h->odd = true;
   h->inst.resize(count);
   for (int k = 0; k < count; k++) {
     Inst I = derive(params[k]);
@@ -1033,11 +1036,11 @@ ij_status ij_autotune(ij_handle h, int reps) {
         if (st != IJ_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return st; }
         const Bucket& b = h->buckets[bi];
         CUDA_TRY(launch_step(h->d_inst, h->d_items + b.first, b.count, nt, b.grid, h->d_t, 0,
-                             false, pf, h->fp16, h->stream));  // warm-up
+                             false, pf, h->fp16, h->odd, h->stream));  // warm-up
         CUDA_TRY(cudaEventRecord(e0, h->stream));
         for (int r = 0; r < reps; r++)
           CUDA_TRY(launch_step(h->d_inst, h->d_items + b.first, b.count, nt, b.grid, h->d_t, 0,
-                               false, pf, h->fp16, h->stream));
+                               false, pf, h->fp16, h->odd, h->stream));
         CUDA_TRY(cudaEventRecord(e1, h->stream));
         CUDA_TRY(cudaEventSynchronize(e1));
         float ms = 0.0f;

@@ -148,7 +148,7 @@ extern "C" ij_status ij_step_noalloc(const ij_params* params, long long t, const
   }
   NOALLOC_TRY(launch_step(d_inst, d_items, n_items, kStepThreads,
                           (n_items + kStepThreads / 32 - 1) / (kStepThreads / 32), d_t, 0, diag,
-                          step_prefetch_for(kStepThreads), false, s));
+                          step_prefetch_for(kStepThreads), false, p.nx % 2 != 0, s));
   if (diag) {
     NOALLOC_TRY(launch_finalize(d_inst, 1, d_t, s));
     NOALLOC_TRY(cudaMemcpyAsync(record_out, base + kOffHist, kRec * sizeof(double),

@@ -46,14 +46,15 @@ struct Inst {
 };
 
 // A unit of work of the step kernel (one warp): `ch` rows starting at y0 of
-// the strip of lattice `inst` that writes columns xs .. xs + nout - 1; lane l
-// holds column xs - halo + l (periodic wrap).
+// the strip of lattice `inst` that writes columns xs .. xs + nout - 1
+// (nout <= 60); lane l holds columns xs - halo + 2 l and the next one
+// (periodic wrap, halo = 2).
 struct Item {
   int inst, xs, nout, halo, y0, ch;
 };
 
 constexpr int kStepThreads = 32;  // one warp per block, one work item each
-constexpr int kStepBlocksPerSM = 16;  // resident blocks per SM (registers: 128 each)
+constexpr int kStepBlocksPerSM = 10;  // resident blocks per SM the registers are sized for
 constexpr int kMaxPrefetch = 4;    // rows staged ahead of use: 1 .. 4
 
 size_t step_smem_bytes(int nthreads, int prefetch, bool h16);
@@ -75,9 +76,11 @@ Inst derive_params(const ij_params& p);
 ij_status report(ij_status st, const char* msg);
 
 cudaError_t launch_init(const Inst* d_inst, const Inst& h_inst, int index, cudaStream_t s);
+// odd: some lattice of the launch has an odd nx (FP32 storage only); its
+// column pairs are then copied and stored one column at a time
 cudaError_t launch_step(const Inst* d_inst, const Item* d_items, int n_items, int nthreads,
                         int grid, const long long* d_t, int t_off, bool diag, int prefetch,
-                        bool h16, cudaStream_t s);
+                        bool h16, bool odd, cudaStream_t s);
 // default number of rows staged ahead of use
 int step_prefetch_for(int nthreads);
 cudaError_t launch_finalize(const Inst* d_inst, int n_inst, const long long* d_t,

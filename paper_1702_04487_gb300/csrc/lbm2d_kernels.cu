@@ -2,16 +2,19 @@
 // (He et al., arXiv:1702.04487, "Methods", Eq. 3-10).
 //
 // Step kernel design (bandwidth-bound stencil, no tensor cores):
-//  - one warp per work item: a strip of 28 written columns (plus two halo
-//    columns each side) by a chunk of rows of one lattice; the warp marches
-//    up the rows, so every cell's populations are read once and written
-//    once per step (structure-of-arrays, coalesced);
-//  - neighbours along x come from warp shuffles, along y from registers;
-//    populations are staged P rows ahead with cp.async into a per-warp ring
-//    in shared memory, and warps never wait on one another;
+//  - one warp per work item: a strip of up to 60 written columns (two
+//    columns per lane, plus two halo columns each side) by a chunk of rows
+//    of one lattice; the warp marches up the rows, so every cell's
+//    populations are read once and written once per step
+//    (structure-of-arrays, 8-byte column pairs, coalesced);
+//  - neighbours along x come from the lane's other column or a warp
+//    shuffle, along y from registers; populations are staged P rows ahead
+//    with cp.async into a per-warp ring in shared memory, and warps never
+//    wait on one another;
 //  - per row iteration: phi of row R, wetting ghost values of row R-1, the
-//    collision of f (Eq. 4-6) and g (Eq. 8-10) on row R-2, the streaming of
-//    row R-3 with halfway bounce-back and the stay/move split of Eq. 8;
+//    collision of f (Eq. 4-6) and g (Eq. 8-10) on row R-2, and the streaming
+//    in push form (halfway bounce-back, the stay/move split of Eq. 8): row
+//    R-3 is completed with the downward movers of row R-2 and stored;
 //  - geometry is analytic (no mask array);
 //  - storage is FP32, or FP16 (f as offsets from w_i n0, g_1..4 as is, g_0
 //    in FP32) with every update in FP32;
@@ -75,21 +78,6 @@ __device__ __forceinline__ bool map_row_v(int y, int ny, int bc, int& ym) {
   }
   return false;
 }
-__device__ __forceinline__ bool near_solid_v(int geom, int bc, int ny, int L, int wt, bool colwall,
-                                             int y) {
-  if (bc == BC_CLOSED && (y == 0 || y == ny - 1)) return true;
-  if (geom == GEOM_NOZZLE) {
-    if (!colwall) return false;
-    if (bc == BC_PER && (y == 0 || y == ny - 1)) return true;
-    return y - 1 < L;
-  }
-  if (geom == GEOM_PLATE) {
-    if (bc == BC_PER && (y == 0 || y == ny - 1)) return true;
-    return y - 1 < wt;
-  }
-  return false;
-}
-
 // Kind of an in-domain cell: 0 fluid, 1 solid, 2 solid on a wetting face.
 __device__ __forceinline__ int geom_kind(const Inst& I, int x, int y) {
   if (I.geom == GEOM_NOZZLE) {
@@ -119,63 +107,43 @@ __device__ __forceinline__ float drive_at(const Inst& I, long long t) {
   return 0.0f;
 }
 
-// Asynchronous 4-byte global -> shared copies (cp.async) of five / four
-// populations p, p + N, ... into shared addresses sa, sa + 128, ... (one
-// population row of a warp apart), issued only when pred is set: one
-// predicate and predicated instructions, no branch.
-__device__ __forceinline__ void cp5_if(unsigned sa, const float* p, int N, bool pred) {
+// Asynchronous global -> shared copies (cp.async), `n` of them: source p +
+// i * N elements, destination sa + i * SS bytes, i = 0 .. n-1.  B bytes per
+// copy (4 or 8).  The caller issues them under a warp-uniform condition.
+template <int B, int SS>
+__device__ __forceinline__ void cp5(unsigned sa, const void* p, size_t strideB) {
+  const char* q = static_cast<const char*>(p);
   asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %6, 0;\n"
-      " @p cp.async.ca.shared.global [%0], [%1], 4;\n"
-      " @p cp.async.ca.shared.global [%0+128], [%2], 4;\n"
-      " @p cp.async.ca.shared.global [%0+256], [%3], 4;\n"
-      " @p cp.async.ca.shared.global [%0+384], [%4], 4;\n"
-      " @p cp.async.ca.shared.global [%0+512], [%5], 4;\n}\n" ::"r"(sa),
-      "l"(p), "l"(p + N), "l"(p + 2 * N), "l"(p + 3 * N), "l"(p + 4 * N), "r"((int)pred)
+      "{\n"
+      " cp.async.ca.shared.global [%0], [%1], %6;\n"
+      " cp.async.ca.shared.global [%0+%7], [%2], %6;\n"
+      " cp.async.ca.shared.global [%0+%8], [%3], %6;\n"
+      " cp.async.ca.shared.global [%0+%9], [%4], %6;\n"
+      " cp.async.ca.shared.global [%0+%10], [%5], %6;\n}\n" ::"r"(sa),
+      "l"(q), "l"(q + strideB), "l"(q + 2 * strideB), "l"(q + 3 * strideB), "l"(q + 4 * strideB),
+      "n"(B), "n"(SS), "n"(2 * SS), "n"(3 * SS), "n"(4 * SS)
       : "memory");
 }
-__device__ __forceinline__ void cp4_if(unsigned sa, const float* p, int N, bool pred) {
+template <int B, int SS>
+__device__ __forceinline__ void cp4(unsigned sa, const void* p, size_t strideB) {
+  const char* q = static_cast<const char*>(p);
   asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %5, 0;\n"
-      " @p cp.async.ca.shared.global [%0], [%1], 4;\n"
-      " @p cp.async.ca.shared.global [%0+128], [%2], 4;\n"
-      " @p cp.async.ca.shared.global [%0+256], [%3], 4;\n"
-      " @p cp.async.ca.shared.global [%0+384], [%4], 4;\n}\n" ::"r"(sa),
-      "l"(p), "l"(p + N), "l"(p + 2 * N), "l"(p + 3 * N), "r"((int)pred)
+      "{\n"
+      " cp.async.ca.shared.global [%0], [%1], %5;\n"
+      " cp.async.ca.shared.global [%0+%6], [%2], %5;\n"
+      " cp.async.ca.shared.global [%0+%7], [%3], %5;\n"
+      " cp.async.ca.shared.global [%0+%8], [%4], %5;\n}\n" ::"r"(sa),
+      "l"(q), "l"(q + strideB), "l"(q + 2 * strideB), "l"(q + 3 * strideB), "n"(B), "n"(SS),
+      "n"(2 * SS), "n"(3 * SS)
       : "memory");
 }
-// FP16 storage: one 4-byte copy, and groups of 4 / 5 copies of the 4-byte
-// half pairs at p, p + N, ... (halves) into sa, sa + DS, ...
+// One predicated copy of B bytes.
+template <int B>
 __device__ __forceinline__ void cp1_if(unsigned sa, const void* p, bool pred) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %2, 0;\n"
-      " @p cp.async.ca.shared.global [%0], [%1], 4;\n}\n" ::"r"(sa),
-      "l"(p), "r"((int)pred)
-      : "memory");
-}
-template <int DS>
-__device__ __forceinline__ void cp4h_if(unsigned sa, const __half* p, int N, bool pred) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %5, 0;\n"
-      " @p cp.async.ca.shared.global [%0], [%1], 4;\n"
-      " @p cp.async.ca.shared.global [%0+%6], [%2], 4;\n"
-      " @p cp.async.ca.shared.global [%0+%7], [%3], 4;\n"
-      " @p cp.async.ca.shared.global [%0+%8], [%4], 4;\n}\n" ::"r"(sa),
-      "l"(p), "l"(p + N), "l"(p + 2 * N), "l"(p + 3 * N), "r"((int)pred), "n"(DS), "n"(2 * DS),
-      "n"(3 * DS)
-      : "memory");
-}
-template <int DS>
-__device__ __forceinline__ void cp5h_if(unsigned sa, const __half* p, int N, bool pred) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %6, 0;\n"
-      " @p cp.async.ca.shared.global [%0], [%1], 4;\n"
-      " @p cp.async.ca.shared.global [%0+%7], [%2], 4;\n"
-      " @p cp.async.ca.shared.global [%0+%8], [%3], 4;\n"
-      " @p cp.async.ca.shared.global [%0+%9], [%4], 4;\n"
-      " @p cp.async.ca.shared.global [%0+%10], [%5], 4;\n}\n" ::"r"(sa),
-      "l"(p), "l"(p + N), "l"(p + 2 * N), "l"(p + 3 * N), "l"(p + 4 * N), "r"((int)pred),
-      "n"(DS), "n"(2 * DS), "n"(3 * DS), "n"(4 * DS)
+      " @p cp.async.ca.shared.global [%0], [%1], %3;\n}\n" ::"r"(sa),
+      "l"(p), "r"((int)pred), "n"(B)
       : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() {
@@ -186,14 +154,6 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// Bit i set when the source x - c_i, y - c_i of direction i is solid.
-__device__ __noinline__ unsigned solid_sources(const Inst& I, int x, int y) {
-  unsigned m = 0;
-  for (int i = 1; i < 9; i++)
-    if (kind_at(I, x - cEX(i), y - cEY(i)) != 0) m |= 1u << i;
-  return m;
-}
-
 // Kind of the in-domain cell (column kind colk, row ym): 0 fluid, 1 solid,
 // 2 solid on a wetting face.  colk is the kind a nozzle-wall column has below
 // y = L (0 for channel and air columns).
@@ -201,6 +161,10 @@ __device__ __forceinline__ int row_kind(int geom, int colk, int L, int wt, int y
   if (geom == GEOM_NOZZLE) return ym < L ? colk : 0;
   if (geom == GEOM_PLATE) return ym < wt ? (ym == wt - 1 ? 2 : 1) : 0;
   return 0;
+}
+// The same for a mapped row m (-1: outside a closed domain, a non-wetting solid).
+__device__ __forceinline__ int kind_m(int geom, int colk, int L, int wt, int m) {
+  return m < 0 ? 1 : row_kind(geom, colk, L, wt, m);
 }
 
 __device__ __forceinline__ int column_kind(const Inst& I, int x) {
@@ -210,78 +174,187 @@ __device__ __forceinline__ int column_kind(const Inst& I, int x) {
   return 0;
 }
 
+// Wetting ghost value of a solid cell of kind k (reading of the wetting
+// boundary condition of "Reproducing the experiment"): the mean over its
+// fluid face neighbours (E, N, W, S) of phi + h_s / kappa (h_s = h on a
+// wetting face, else 0); a solid cell touching fluid only diagonally takes
+// the plain mean of those diagonal neighbours (NE, NW, SW, SE).
+__device__ __forceinline__ float ghost_phi(int k, float hk, float pE, int kE, float pN, int kN,
+                                           float pW, int kW, float pS, int kS, float pNE, int kNE,
+                                           float pNW, int kNW, float pSW, int kSW, float pSE,
+                                           int kSE) {
+  const float h = k == 2 ? hk : 0.0f;
+  float sum = 0.0f;
+  int cnt = 0;
+  if (kE == 0) { sum += pE + h; cnt++; }
+  if (kN == 0) { sum += pN + h; cnt++; }
+  if (kW == 0) { sum += pW + h; cnt++; }
+  if (kS == 0) { sum += pS + h; cnt++; }
+  if (cnt == 0) {
+    if (kNE == 0) { sum += pNE; cnt++; }
+    if (kNW == 0) { sum += pNW; cnt++; }
+    if (kSW == 0) { sum += pSW; cnt++; }
+    if (kSE == 0) { sum += pSE; cnt++; }
+  }
+  return cnt ? sum / (float)cnt : 0.0f;
+}
+
+// Per-lattice constants of the collision, in registers.
+struct CollK {
+  float phis, inv_phis, A4, kappa, omq, inv_tphi, gamma, inv2q, qmt, nu_air, dnu, n0, Fd;
+};
+
+// Collision of one fluid cell (Eq. 4-6 for f, Eq. 8-10 for g).
+//  fr: f_i - w_i n0 of the cell; g: g_i; phi = sum g (raw); pC .. pSE: phi
+//  with wetting ghosts of the cell and its 8 neighbours.
+//  Out: fs = post-collision f_i - w_i n0 (i = 0..8); gP[i-1] = q g_i +
+//  Omega_i (the part that moves, i = 1..4); gS[i-1] = (1 - q) g_i (the part
+//  that stays); g0n = g_0 + Omega_0; n, uy, u2 of the cell.
+__device__ __forceinline__ void collide_cell(const float (&fr)[9], const float (&g)[5], float phi,
+                                             float pC, float pE, float pN, float pW, float pS,
+                                             float pNE, float pNW, float pSW, float pSE,
+                                             bool driven, const CollK& K, float (&fs)[9],
+                                             float (&gP)[4], float (&gS)[4], float& g0n, float& n,
+                                             float& uy, float& u2) {
+  // lap = 6 sum_i w_i (phi_i - phi) from the differences, which are exact
+  // where neighbours are close (no cancellation of O(10) terms)
+  const float lap = (2.0f / 3.0f) * ((pE - pC) + (pN - pC) + (pW - pC) + (pS - pC)) +
+                    (1.0f / 6.0f) * ((pNE - pC) + (pNW - pC) + (pSW - pC) + (pSE - pC));
+  const float gx = (pE - pW) * (1.0f / 3.0f) + (pNE - pNW - pSW + pSE) * (1.0f / 12.0f);
+  const float gy = (pN - pS) * (1.0f / 3.0f) + (pNE + pNW - pSW - pSE) * (1.0f / 12.0f);
+  const float mu = K.A4 * phi * ((phi - K.phis) * (phi + K.phis)) - K.kappa * lap;
+  float C = 0.5f * (phi * K.inv_phis + 1.0f);
+  C = fminf(fmaxf(C, 0.0f), 1.0f);
+  const float Fb = driven ? K.Fd * C : 0.0f;
+  const float Fx = mu * gx, Fy = mu * gy + Fb;
+  // fr holds deviations f_i - w_i n0: their sum is n - n0
+  const float dn = fr[0] + fr[1] + fr[2] + fr[3] + fr[4] + fr[5] + fr[6] + fr[7] + fr[8];
+  n = K.n0 + dn;
+  const float mx = fr[1] - fr[3] + fr[5] - fr[6] - fr[7] + fr[8];
+  const float my = fr[2] - fr[4] + fr[5] + fr[6] - fr[7] - fr[8];
+  const float inv_n = __frcp_rn(n);  // 1 / n, correctly rounded
+  const float ux = (mx + 0.5f * Fx) * inv_n;
+  uy = (my + 0.5f * Fy) * inv_n;
+  u2 = ux * ux + uy * uy;
+  const float om = __frcp_rn(0.5f + 3.0f * (K.nu_air + C * K.dnu));
+  const float pref = 3.0f * (1.0f - 0.5f * om);
+  // A_i - n0 = 3 (phi mu + n / 3) - n0 for i >= 1 (Eq. 6), on deviations
+  const float p3 = dn + 3.0f * phi * mu;
+  const float uF = ux * Fx + uy * Fy;
+  const float base = -1.5f * u2;  // velocity-independent part of the bracket of Eq. 5
+  // Moving directions first (deviations feq_i - w_i n0); the rest direction
+  // then takes the balance, feq_0 - w_0 n0 = (n - n0) - sum_{i>=1} (feq_i -
+  // w_i n0) and F_0 = -sum_{i>=1} F_i.  This equals A_0 of Eq. 6 (the
+  // moments of Eq. 5-6 and of the forcing term are exact) but conserves
+  // mass in FP32, whose rounded weights 4/9, 1/9, 1/36 do not sum to one.
+  // Opposite directions i, i' share the even part of the equilibrium and of
+  // the forcing term and differ in the sign of the odd part: feq = E +- O,
+  // F = FE +- FO with E = w (p3 + n (base + 4.5 cu^2)), O = 3 w n cu,
+  // FE = w pref (3 cu cF - uF), FO = w pref cF.  The collision
+  // f* = (1 - om) f + om feq + F then reads f*_i = (1 - om) f_i + A +- B
+  // with A = om E + FE and B = om O + FO.
+  float sumA = 0.0f;
+  const float omc = 1.0f - om, on3 = om * 3.0f * n;
+#pragma unroll
+  for (int i = 1; i < 9; i++) {
+    if (i == 3 || i == 4 || i == 7 || i == 8) continue;  // handled with its pair
+    const int ib = i == 1 ? 3 : (i == 2 ? 4 : (i == 5 ? 7 : 8));
+    const float w = i < 5 ? W1 : W2;
+    const float ex = (float)cEX(i), ey = (float)cEY(i);
+    const float cu = ex * ux + ey * uy;
+    const float cF = ex * Fx + ey * Fy;
+    const float E = w * fmaf(n, fmaf(4.5f * cu, cu, base), p3);
+    const float wp = w * pref;
+    const float FE = wp * fmaf(3.0f * cu, cF, -uF);
+    const float A = fmaf(om, E, FE);
+    const float B = fmaf(w * on3, cu, wp * cF);
+    sumA += A;
+    fs[i] = fmaf(omc, fr[i], A + B);
+    fs[ib] = fmaf(omc, fr[ib], A - B);
+  }
+  fs[0] = fmaf(omc, fr[0], fmaf(om, dn, -2.0f * sumA));
+  // order parameter: Eq. 9-10 with the rest direction special; the moving
+  // part q g_i + Omega_i streams, (1 - q) g_i stays
+  const float gmu = K.gamma * mu;
+  const float pq = phi * K.inv2q;
+  float sum_ge = 0.0f;
+#pragma unroll
+  for (int i = 1; i < 5; i++) {
+    const float cu = (float)cEX(i) * ux + (float)cEY(i) * uy;
+    const float ge = 0.5f * gmu + pq * cu;
+    sum_ge += ge;
+    gP[i - 1] = fmaf(K.qmt, g[i], ge * K.inv_tphi);  // q g + (ge - g) / tau_phi
+    gS[i - 1] = K.omq * g[i];
+  }
+  // rest direction: g0_0 = phi - sum_{i>=1} g0_i (Eq. 10 as a balance, so
+  // that sum g0 = phi exactly); with phi - g_0 = sum_{i>=1} g_i the
+  // relaxation uses small terms only
+  g0n = g[0] + ((g[1] + g[2] + g[3] + g[4]) - sum_ge) * K.inv_tphi;
+}
+
 // ---------------------------------------------------------------------------
 // The fused step: one warp per work item (a strip of columns x a chunk of
 // rows of one lattice); warps never wait on one another.
 //
-// Lane l of a strip holds column x = xs - 2 + l (periodic wrap).  The strip
-// writes the nout <= 28 columns of lanes 2 .. nout+1; lanes 1 and nout+2
-// collide too (the streaming pulls their post-collision populations), and
-// lanes 0 and 31 only contribute phi to the stencil.  When lane 0 or 31
-// sits on a wall, its ghost value needs phi beyond the strip: that lane
-// stages the g of the column outside as well.  Neighbours along x are
-// exchanged with warp shuffles; along y each lane keeps its own column's
-// last rows in registers while the warp marches up the rows.
+// Lane l holds two neighbouring columns, A = xs - 2 + 2 l and B = A + 1
+// (periodic wrap).  The strip writes the nout <= 60 columns xs .. xs+nout-1
+// (lanes 1..30 when nout = 60); columns xs - 1 and xs + nout collide too
+// (their populations stream into the strip), and xs - 2, xs + nout + 1 only
+// give phi to the stencil.  A solid edge column (lane 0's A, lane 31's B)
+// needs phi beyond the strip for its ghost value: that lane also stages the
+// g of the column outside.  Neighbours along x: the other column of the lane,
+// or the neighbouring lane's by warp shuffle; along y: registers, as the warp
+// marches up the rows.
 //
-// Per row iteration (pipeline row R): phi of row R (sum of g); the wetting
-// ghost values of row R-1 (only rows with a solid cell in the strip); the
-// collision of row R-2 (Eq. 4-6 for f, Eq. 8-10 for g); the streaming of
-// row R-3 with halfway bounce-back and the stay/move split of Eq. 8, stored
-// to the other time buffer.  Every lane stages its own column's 14
-// populations of row R+P into the warp's shared-memory ring with cp.async,
-// P rows ahead of use, and reads back only what it staged itself.
+// Per row iteration (pipeline row R): raw phi of row R (sum of g); wetting
+// ghosts of row R-1 (rows with a solid cell in the warp only); the collision
+// of row R-2 (Eq. 4-6 and 8-10); then the streaming in push form: row R-3,
+// whose in-row and upward pulls were gathered when row R-3 collided, takes
+// the downward movers of row R-2 and is stored; row R-2's own pulls (rest,
+// sideways movers, stay parts, the upward movers of row R-3) are gathered
+// into the same registers.  A pull whose source is solid takes the cell's
+// own post-collision population of the opposite direction (halfway
+// bounce-back; the moving g part likewise returns, conserving mass).
 //
-// FP16 storage (H): a cp.async moves 4 bytes at least, so each even lane
-// stages the half pair of its own column and the next (x even: strips start
-// at even columns and nx is even, so a pair never straddles the wrap); every
-// lane stages its FP32 g_0; the edge lanes stage the outer column's g into
-// slots of their own.  One staged row holds (in 4-byte words) g_0[32],
-// g_1..4 as [4][16] half pairs, f_0..8 as [9][16] half pairs, then the outer
-// g_0 and g_1..4 pairs of lane 0 and of lane 31.
-constexpr int kWarpsPerBlock = kStepThreads / 32;
-constexpr int kRowFloats = 14 * 32;  // one staged row of a warp: g[5][32], then f[9][32]
-constexpr int kRowWordsH = 256;      // the same in FP16 storage (250 used)
+// Staging: each lane copies its own column pair with cp.async into a
+// per-warp ring in shared memory and reads back only what it copied: g of
+// row R+P (ring of P+3 rows) and f of row R+P-2 (ring of P+1 rows, f is
+// needed at the collision only), as one group per row.  FP32: 8-byte copies
+// of (A, B), which are contiguous and 8-byte aligned when nx is even (ODD
+// instantiation: two 4-byte copies).  FP16 storage: 4-byte half pairs of f
+// and g_1..4, 8-byte FP32 pairs of g_0; every update in FP32.
+constexpr int kStripCols = 60;  // written columns of one work item
 constexpr unsigned kFull = 0xffffffffu;
 
-template <bool DIAG, int P, bool H>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, kStepBlocksPerSM)
+template <int P, bool H>
+struct StepRing {
+  static constexpr int DG = P + 3;  // g rows R+P .. R-2
+  static constexpr int DF = P + 1;  // f rows R+P-2 .. R-2
+  // words (4 bytes) of one row: FP32 g [5][64], f [9][64]; FP16 g_0 [64]
+  // FP32 then g_1..4 [4][32] half pairs, f [9][32] half pairs
+  static constexpr int GW = H ? 192 : 320;
+  static constexpr int FW = H ? 288 : 576;
+  // outer column of the edge lanes: [lane 0, lane 31][5 values, 2 words each]
+  static constexpr int OW = 20;
+};
+
+template <bool DIAG, int P, bool H, bool ODD>
+__global__ void __launch_bounds__(32, kStepBlocksPerSM)
     step_kernel(const Inst* __restrict__ insts, const Item* __restrict__ items, int n_items,
                 const long long* __restrict__ d_t, int t_off) {
-  constexpr int D = P + 3;  // ring rows: R+P .. R-2 are live
-  constexpr int kRowW = H ? kRowWordsH : kRowFloats;
+  using RG = StepRing<P, H>;
+  static_assert(!(H && ODD), "FP16 storage needs an even nx");
   extern __shared__ float4 smem4[];
-  // with one warp per block the warp index is the constant 0, so the compiler
-  // sees the work item, its lattice and the row loop as warp-uniform
-  const int lane = threadIdx.x & 31, warp = kWarpsPerBlock == 1 ? 0 : threadIdx.x >> 5;
-  // FP32: each lane's column of the ring; FP16: the warp's ring
-  float* ring = reinterpret_cast<float*>(smem4) + warp * D * kRowW + (H ? 0 : lane);
-  const unsigned ring_sa = (unsigned)__cvta_generic_to_shared(ring);
+  float* const sg = reinterpret_cast<float*>(smem4);  // g ring
+  float* const so = sg + RG::DG * RG::GW;              // outer-column ring
+  float* const sf = so + RG::DG * RG::OW;              // f ring
+  const unsigned sg_a = (unsigned)__cvta_generic_to_shared(sg);
+  const unsigned so_a = (unsigned)__cvta_generic_to_shared(so);
+  const unsigned sf_a = (unsigned)__cvta_generic_to_shared(sf);
+  const int lane = threadIdx.x;
   const long long t = *d_t + t_off;
-  // staged g_i / f_i of this lane's column, and the sum of the outer g
-  auto ring_g = [&](const float* row, int i) -> float {
-    if (!H) return row[i * 32];
-    if (i == 0) return row[lane];
-    return __half2float(reinterpret_cast<const __half*>(row + 32 + (i - 1) * 16)[lane]);
-  };
-  auto ring_f = [&](const float* row, int i) -> float {
-    if (!H) return row[(5 + i) * 32];
-    return __half2float(reinterpret_cast<const __half*>(row + 96 + i * 16)[lane]);
-  };
-  auto ring_outer = [&](const float* row) -> float {
-    if (!H) return row[160] + row[192] + row[224] + row[256] + row[288];
-    // lane 0: outer column x - 1 is odd, the upper half; lane 31: x + 1 even
-    const float* o = row + 240 + (lane == 0 ? 0 : 5);
-    float sum = o[0];
-#pragma unroll
-    for (int i = 1; i < 5; i++) {
-      const __half2 hp = reinterpret_cast<const __half2*>(o)[i];
-      sum += lane == 0 ? __high2float(hp) : __low2float(hp);
-    }
-    return sum;
-  };
 
-  for (int item = blockIdx.x * kWarpsPerBlock + warp; item < n_items;
-       item += gridDim.x * kWarpsPerBlock) {
+  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
     const Item it = items[item];
     const Inst& I = insts[it.inst];
     // a lattice whose numeric flag is set is frozen
@@ -290,377 +363,416 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kStepBlocksPerSM)
     const int nx = I.nx, ny = I.ny, geom = I.geom, L = I.L, wt = I.wt, bc = I.bc;
     const int N = nx * ny;  // < 2^31 / 9 (checked on the host)
     const int y0 = it.y0, ch = it.ch;
-    const int x = wrapi(it.xs - it.halo + lane, nx);
-    const bool out_lane = lane >= it.halo && lane < it.halo + it.nout;
-    const bool col_lane = lane >= it.halo - 1 && lane <= it.halo + it.nout;
-    const int ck = column_kind(I, x);
-    const int ckW = column_kind(I, wrapi(x - 1, nx)), ckE = column_kind(I, wrapi(x + 1, nx));
-    const bool colwall = geom == GEOM_NOZZLE && (ck | ckW | ckE) != 0;
-    // lanes 0 and 31 on a wall column: the column outside the strip (xo)
-    const bool edge = (lane == 0 || lane == 31) && ck != 0;
-    const int xo = wrapi(lane == 0 ? x - 1 : x + 1, nx);
-    const int cko = lane == 0 ? ckW : ckE;
-    const bool drive_col = geom != GEOM_NOZZLE || (x >= I.cx0 && x < I.cx1);
-    const float phis = I.phis, inv_phis = I.inv_phis, A4 = I.A4, kappa = I.kappa, hk = I.hk;
-    const float omq = I.omq, inv_tphi = I.inv_tphi, gamma = I.gamma, inv2q = I.inv2q;
-    const float qmt = I.q - I.inv_tphi;
-    const float nu_air = I.nu_air, dnu = I.dnu, n0 = I.n0;
-    const float Fd = drive_at(I, t);
+    const int uA = it.xs - 2 + 2 * lane, uB = uA + 1;  // unwrapped columns
+    const int xA = wrapi(uA, nx), xB = wrapi(uB, nx);
+    const int ckA = column_kind(I, xA), ckB = column_kind(I, xB);
+    const int ckW = column_kind(I, wrapi(uA - 1, nx));  // west of A
+    const int ckE = column_kind(I, wrapi(uB + 1, nx));  // east of B
+    // lanes whose cells or neighbours may be solid (bounce-back, ghosts)
+    const bool colmay = geom == GEOM_PLATE || (geom == GEOM_NOZZLE && (ckW | ckA | ckB | ckE) != 0);
+    // lane 0's A / lane 31's B on a wall column: the column outside (xo)
+    const bool edge = (lane == 0 && ckA != 0) || (lane == 31 && ckB != 0);
+    const int xo = lane == 0 ? wrapi(uA - 1, nx) : wrapi(uB + 1, nx);
+    const int cko = lane == 0 ? ckW : ckE, cke = lane == 0 ? ckA : ckB;
+    const bool any_edge = __any_sync(kFull, edge);
+    const bool dA = geom != GEOM_NOZZLE || (xA >= I.cx0 && xA < I.cx1);
+    const bool dB = geom != GEOM_NOZZLE || (xB >= I.cx0 && xB < I.cx1);
+    const int xe = it.xs + it.nout;
+    const bool vA = uA >= it.xs - 1 && uA <= xe, vB = uB >= it.xs - 1 && uB <= xe;  // results used
+    const bool wA = uA >= it.xs && uA < xe, wB = uB >= it.xs && uB < xe;            // written
+    CollK K;
+    K.phis = I.phis;
+    K.inv_phis = I.inv_phis;
+    K.A4 = I.A4;
+    K.kappa = I.kappa;
+    K.omq = I.omq;
+    K.inv_tphi = I.inv_tphi;
+    K.gamma = I.gamma;
+    K.inv2q = I.inv2q;
+    K.qmt = I.q - I.inv_tphi;
+    K.nu_air = I.nu_air;
+    K.dnu = I.dnu;
+    K.n0 = I.n0;
+    K.Fd = drive_at(I, t);
+    const float hk = I.hk;
     const float* __restrict__ fin = I.f[t & 1];
     const float* __restrict__ gin = I.g[t & 1];
     float* __restrict__ fout = I.f[(t + 1) & 1];
     float* __restrict__ gout = I.g[(t + 1) & 1];
-    // FP16 storage: f halves; g_0 FP32 [N], then g_1..4 halves [4][N]
+    // FP16 storage: f halves [9][N]; g_0 FP32 [N], then g_1..4 halves [4][N]
     const __half* __restrict__ fhin = reinterpret_cast<const __half*>(fin);
     const __half* __restrict__ ghin = reinterpret_cast<const __half*>(gin + N);
     __half* __restrict__ fhout = reinterpret_cast<__half*>(fout);
     __half* __restrict__ ghout = reinterpret_cast<__half*>(gout + N);
-    const bool any_edge = H && __any_sync(kFull, edge);
 
-    // Stage pipeline row r into ring slot sp (the lane's own column, or in
-    // FP16 storage the pair of columns of an even lane; f only for rows that
-    // are collided), as one cp.async group.
-    auto stage = [&](int r, int sp) {
+    // Stage g of row rg into g slot sgs and f of row rf into f slot sfs (one
+    // cp.async group; rows outside the item's needs or a closed domain are
+    // skipped, warp-uniformly).
+    auto stage = [&](int rg, int sgs, int rf, int sfs) {
       int ym;
-      if (r <= y0 + ch + 2 && map_row_v(r, ny, bc, ym)) {  // uniform over the warp
-        const unsigned d = ring_sa + sp * (kRowW * 4);
-        const bool own = row_kind(geom, ck, L, wt, ym) == 0;
-        const bool frow = r >= y0 - 1 && r <= y0 + ch;
-        // a solid edge lane with a fluid cell beyond the strip stages that
-        // cell's g (FP32: where its own f would be; FP16: slots of its own)
-        const bool outer = edge && !own && row_kind(geom, cko, L, wt, ym) == 0;
-        if (!H) {
-          const bool fneed = own && col_lane && frow;
-          const float* qg = gin + (ym * nx + x);
-          const float* qf = outer ? gin + (ym * nx + xo) : fin + (ym * nx + x);
-          cp5_if(d, qg, N, own);
-          cp5_if(d + 5 * 128, qf, N, fneed || outer);
-          cp4_if(d + 10 * 128, qf + 5 * N, N, fneed);
+      if (rg <= y0 + ch + 2 && map_row_v(rg, ny, bc, ym)) {
+        const unsigned d = sg_a + sgs * (RG::GW * 4);
+        const int c = ym * nx + xA;
+        if (ODD) {
+          cp5<4, 256>(d + lane * 8, gin + c, (size_t)N * 4);
+          cp5<4, 256>(d + lane * 8 + 4, gin + ym * nx + xB, (size_t)N * 4);
+        } else if (!H) {
+          cp5<8, 256>(d + lane * 8, gin + c, (size_t)N * 4);
         } else {
-          const int c = ym * nx + x;
-          cp1_if(d + lane * 4, gin + c, own);
-          // the even lane of a pair copies for both (x + 1 has kind ckE)
-          const bool pair = (lane & 1) == 0 && (own || row_kind(geom, ckE, L, wt, ym) == 0);
-          const bool fpair = pair && frow && lane <= it.halo + it.nout;
-          const unsigned dp = d + (lane >> 1) * 4;
-          cp4h_if<64>(dp + 128, ghin + c, N, pair);
-          cp5h_if<64>(dp + 384, fhin + c, N, fpair);
-          cp4h_if<64>(dp + 384 + 5 * 64, fhin + 5 * N + c, N, fpair);
-          if (any_edge) {
-            const int co = ym * nx + xo;
-            const unsigned dq = d + 960 + (lane == 0 ? 0 : 20);
-            cp1_if(dq, gin + co, outer);
-            cp4h_if<4>(dq + 4, ghin + (co & ~1), N, outer);
+          cp1_if<8>(d + lane * 8, gin + c, true);
+          cp4<4, 128>(d + 256 + lane * 4, ghin + c, (size_t)N * 2);
+        }
+        if (any_edge) {
+          // a solid edge column next to a fluid one outside the strip
+          const bool need = edge && row_kind(geom, cke, L, wt, ym) != 0 &&
+                            row_kind(geom, cko, L, wt, ym) == 0;
+          const unsigned o = so_a + sgs * (RG::OW * 4) + (lane == 0 ? 0 : 40);
+          const int co = ym * nx + (ODD ? xo : (xo & ~1));
+          if (!H) {
+#pragma unroll
+            for (int i = 0; i < 5; i++)
+              cp1_if<ODD ? 4 : 8>(o + i * 8, gin + (size_t)i * N + co, need);
+          } else {
+            cp1_if<8>(o, gin + co, need);
+#pragma unroll
+            for (int i = 1; i < 5; i++)
+              cp1_if<4>(o + i * 8, ghin + (size_t)(i - 1) * N + co, need);
           }
+        }
+      }
+      if (rf >= y0 - 1 && rf <= y0 + ch && map_row_v(rf, ny, bc, ym)) {
+        const unsigned d = sf_a + sfs * (RG::FW * 4);
+        const int c = ym * nx + xA;
+        if (ODD) {
+          cp5<4, 256>(d + lane * 8, fin + c, (size_t)N * 4);
+          cp4<4, 256>(d + 5 * 256 + lane * 8, fin + 5 * (size_t)N + c, (size_t)N * 4);
+          const int cb = ym * nx + xB;
+          cp5<4, 256>(d + lane * 8 + 4, fin + cb, (size_t)N * 4);
+          cp4<4, 256>(d + 5 * 256 + lane * 8 + 4, fin + 5 * (size_t)N + cb, (size_t)N * 4);
+        } else if (!H) {
+          cp5<8, 256>(d + lane * 8, fin + c, (size_t)N * 4);
+          cp4<8, 256>(d + 5 * 256 + lane * 8, fin + 5 * (size_t)N + c, (size_t)N * 4);
+        } else {
+          cp5<4, 128>(d + lane * 4, fhin + c, (size_t)N * 2);
+          cp4<4, 128>(d + 5 * 128 + lane * 4, fhin + 5 * (size_t)N + c, (size_t)N * 2);
         }
       }
       cp_async_commit();
     };
+    // staged values of this lane: g_i / f_i of columns A and B of a slot
+    auto load_g = [&](int slot, float (&a)[5], float (&b)[5]) {
+      const float* r = sg + slot * RG::GW;
+      if (!H) {
 #pragma unroll
-    for (int j = 0; j < P; j++) stage(y0 - 3 + j, j);
+        for (int i = 0; i < 5; i++) {
+          const float2 v = reinterpret_cast<const float2*>(r + i * 64)[lane];
+          a[i] = v.x;
+          b[i] = v.y;
+        }
+      } else {
+        const float2 v = reinterpret_cast<const float2*>(r)[lane];
+        a[0] = v.x;
+        b[0] = v.y;
+#pragma unroll
+        for (int i = 1; i < 5; i++) {
+          const float2 w = __half22float2(reinterpret_cast<const __half2*>(r + 64 + (i - 1) * 32)[lane]);
+          a[i] = w.x;
+          b[i] = w.y;
+        }
+      }
+    };
+    auto load_f = [&](int slot, float (&a)[9], float (&b)[9]) {
+      const float* r = sf + slot * RG::FW;
+#pragma unroll
+      for (int i = 0; i < 9; i++) {
+        float2 v;
+        if (!H)
+          v = reinterpret_cast<const float2*>(r + i * 64)[lane];
+        else
+          v = __half22float2(reinterpret_cast<const __half2*>(r + i * 32)[lane]);
+        a[i] = v.x;
+        b[i] = v.y;
+      }
+    };
+    // raw phi of the outer column (edge lanes)
+    auto load_outer = [&](int slot) -> float {
+      const float* o = so + slot * RG::OW + (lane == 0 ? 0 : 10);
+      const int wd = (ODD || lane == 31) ? 0 : 1;  // lane 0: the odd column of its pair
+      if (!H) return o[wd] + o[2 + wd] + o[4 + wd] + o[6 + wd] + o[8 + wd];
+      float s = o[wd];
+#pragma unroll
+      for (int i = 1; i < 5; i++) {
+        const __half2 hp = *reinterpret_cast<const __half2*>(o + 2 * i);
+        s += wd ? __high2float(hp) : __low2float(hp);
+      }
+      return s;
+    };
 
-    // per pipeline row of the own column: raw phi of rows R, R-1, R-2
-    // (pr0..pr2), phi with ghosts of rows R-1, R-2, R-3 (pe0..pe2), kinds of
-    // rows R .. R-3 (k0..k3), mapped rows R .. R-2 (m0..m2; -1 outside a
-    // closed domain)
-    float pr0 = 0.f, pr1 = 0.f, pr2 = 0.f, pe0 = 0.f, pe1 = 0.f, pe2 = 0.f;
-    float px0 = 0.f, px1 = 0.f, px2 = 0.f;  // raw phi outside the strip (edge lanes)
-    int k0 = 1, k1 = 1, k2 = 1, k3 = 1;
-    int m0 = -1, m1 = -1, m2 = -1;
-    // post-collision f_1..8 and moving g parts P_1..4 of row R-3 (cB); of
-    // row R-4 only what the pull takes from it: f*_2, f*_5, f*_6, P_2 (cA);
-    // rest f_0*, g_0* and stay parts (1-q) g_1..4 of row R-3 (oB)
-    float cA[4], cB[12], oB[6];
 #pragma unroll
-    for (int i = 0; i < 4; i++) cA[i] = 0.f;
+    for (int j = 0; j < P; j++) stage(y0 - 3 + j, j, y0 - 5 + j, j);
+
+    // raw phi of rows R, R-1, R-2 (pr*0..2) and of the outer column (px*);
+    // phi with ghosts of rows R-1, R-2, R-3 (pe*0..2) and of the columns
+    // west of A (peW*) and east of B (peE*); mapped rows R .. R-3 (m0..m3)
+    float prA0 = 0.f, prA1 = 0.f, prA2 = 0.f, prB0 = 0.f, prB1 = 0.f, prB2 = 0.f;
+    float px0 = 0.f, px1 = 0.f, px2 = 0.f;
+    float peA0 = 0.f, peA1 = 0.f, peA2 = 0.f, peB0 = 0.f, peB1 = 0.f, peB2 = 0.f;
+    float peW0 = 0.f, peW1 = 0.f, peW2 = 0.f, peE0 = 0.f, peE1 = 0.f, peE2 = 0.f;
+    int m0 = -1, m1 = -1, m2 = -1, m3 = -1;
+    // gathered pulls of the row being streamed, per column: f_0..3, f_5,
+    // f_6 and g_0..4 (g_4 without its moving part yet); the upward movers
+    // for the next row (f_2 own, f_5 from the west, f_6 from the east, the
+    // moving g_2 own); own f*_5, f*_6 (bounce-back of f_7, f_8)
+    float aA[11], aB[11], upA[4], upB[4], bbA[2], bbB[2];
 #pragma unroll
-    for (int i = 0; i < 12; i++) cB[i] = 0.f;
+    for (int i = 0; i < 11; i++) aA[i] = aB[i] = 0.f;
 #pragma unroll
-    for (int i = 0; i < 6; i++) oB[i] = 0.f;
-    // the new row's values: lanes that do not collide keep the last ones
-    // (never read: their pulling neighbours bounce back)
-    float cn[12], on[6];
-#pragma unroll
-    for (int i = 0; i < 12; i++) cn[i] = 0.f;
-#pragma unroll
-    for (int i = 0; i < 6; i++) on[i] = 0.f;
+    for (int i = 0; i < 4; i++) upA[i] = upB[i] = 0.f;
+    bbA[0] = bbA[1] = bbB[0] = bbB[1] = 0.f;
     double acc_n = 0.0, acc_phi = 0.0, acc_mom = 0.0;
-    int sl = 0;  // ring slot of row R
+    int gr = 0, gw = P, fr_ = 0, fw = P;  // ring slots: g of row R / R+P, f of row R-2 / R+P-2
+    if (gw >= RG::DG) gw -= RG::DG;
+    if (fw >= RG::DF) fw -= RG::DF;
 
 #pragma unroll 1
     for (int k = 0; k < ch + 6; k++) {
       const int R = y0 - 3 + k;
-      {
-        int sp = sl + P;
-        if (sp >= D) sp -= D;  // the slot of row R+P is the slot of row R-3
-        stage(R + P, sp);
-      }
-      cp_async_wait<P>();  // this lane's copies of row R have landed
-      k3 = k2;
-      k2 = k1;
-      k1 = k0;
+      stage(R + P, gw, R + P - 2, fw);
+      cp_async_wait<P>();  // this lane's copies of g row R and f row R-2 have landed
+      m3 = m2;
       m2 = m1;
       m1 = m0;
-      pr2 = pr1;
-      pr1 = pr0;
-      px2 = px1;
-      px1 = px0;
-      pe2 = pe1;
-      pe1 = pe0;
       {
         int ym;
         m0 = map_row_v(R, ny, bc, ym) ? ym : -1;
-        k0 = m0 >= 0 ? row_kind(geom, ck, L, wt, m0) : 1;
-        const float* sg = ring + sl * kRowW;
-        pr0 = k0 == 0 ? ring_g(sg, 0) + ring_g(sg, 1) + ring_g(sg, 2) + ring_g(sg, 3) +
-                            ring_g(sg, 4)
-                      : 0.0f;
-        px0 = edge && k0 != 0 && m0 >= 0 && row_kind(geom, cko, L, wt, m0) == 0
-                  ? ring_outer(sg)
-                  : 0.0f;
+      }
+      prA2 = prA1; prA1 = prA0; prB2 = prB1; prB1 = prB0;
+      px2 = px1; px1 = px0;
+      peA2 = peA1; peA1 = peA0; peB2 = peB1; peB1 = peB0;
+      peW2 = peW1; peW1 = peW0; peE2 = peE1; peE1 = peE0;
+      const int kA0 = kind_m(geom, ckA, L, wt, m0), kB0 = kind_m(geom, ckB, L, wt, m0);
+      const int kA1 = kind_m(geom, ckA, L, wt, m1), kB1 = kind_m(geom, ckB, L, wt, m1);
+      // ---- raw phi of row R
+      {
+        float ga[5], gb[5];
+        load_g(gr, ga, gb);
+        prA0 = kA0 == 0 ? ga[0] + ga[1] + ga[2] + ga[3] + ga[4] : 0.0f;
+        prB0 = kB0 == 0 ? gb[0] + gb[1] + gb[2] + gb[3] + gb[4] : 0.0f;
+        px0 = 0.0f;
+        if (any_edge && edge && m0 >= 0 && row_kind(geom, cke, L, wt, m0) != 0 &&
+            row_kind(geom, cko, L, wt, m0) == 0)
+          px0 = load_outer(gr);
       }
       // ---- phi with wetting ghosts of row R-1
-      pe0 = pr1;
-      if (__any_sync(kFull, k1 != 0)) {
-        float aW = __shfl_up_sync(kFull, pr0, 1), aE = __shfl_down_sync(kFull, pr0, 1);
-        float bW = __shfl_up_sync(kFull, pr1, 1), bE = __shfl_down_sync(kFull, pr1, 1);
-        float cW = __shfl_up_sync(kFull, pr2, 1), cE = __shfl_down_sync(kFull, pr2, 1);
+      peA0 = prA1;
+      peB0 = prB1;
+      if (__any_sync(kFull, (kA1 | kB1) != 0)) {
+        float wN = __shfl_up_sync(kFull, prB0, 1), wC = __shfl_up_sync(kFull, prB1, 1);
+        float wS = __shfl_up_sync(kFull, prB2, 1);
+        float eN = __shfl_down_sync(kFull, prA0, 1), eC = __shfl_down_sync(kFull, prA1, 1);
+        float eS = __shfl_down_sync(kFull, prA2, 1);
         if (edge && lane == 0) {
-          aW = px0;
-          bW = px1;
-          cW = px2;
+          wN = px0; wC = px1; wS = px2;
         } else if (edge) {
-          aE = px0;
-          bE = px1;
-          cE = px2;
+          eN = px0; eC = px1; eS = px2;
         }
-        if (k1 != 0) {
-          // kinds of the neighbours in rows R (a), R-1 (b), R-2 (c)
-          const int kaW = m0 >= 0 ? row_kind(geom, ckW, L, wt, m0) : 1;
-          const int kaE = m0 >= 0 ? row_kind(geom, ckE, L, wt, m0) : 1;
-          const int kbW = m1 >= 0 ? row_kind(geom, ckW, L, wt, m1) : 1;
-          const int kbE = m1 >= 0 ? row_kind(geom, ckE, L, wt, m1) : 1;
-          const int kcW = m2 >= 0 ? row_kind(geom, ckW, L, wt, m2) : 1;
-          const int kcE = m2 >= 0 ? row_kind(geom, ckE, L, wt, m2) : 1;
-          // mean over fluid face neighbours of phi + h_s / kappa, else the
-          // plain mean over fluid diagonal neighbours
-          const float h = k1 == 2 ? hk : 0.0f;
-          float sum = 0.0f;
-          int cnt = 0;
-          if (kbE == 0) { sum += bE + h; cnt++; }
-          if (k0 == 0) { sum += pr0 + h; cnt++; }
-          if (kbW == 0) { sum += bW + h; cnt++; }
-          if (k2 == 0) { sum += pr2 + h; cnt++; }
-          if (cnt == 0) {
-            if (kaE == 0) { sum += aE; cnt++; }
-            if (kaW == 0) { sum += aW; cnt++; }
-            if (kcW == 0) { sum += cW; cnt++; }
-            if (kcE == 0) { sum += cE; cnt++; }
-          }
-          pe0 = cnt ? sum / (float)cnt : 0.0f;
-        }
+        const int kA2 = kind_m(geom, ckA, L, wt, m2), kB2 = kind_m(geom, ckB, L, wt, m2);
+        const int kW0 = kind_m(geom, ckW, L, wt, m0), kW1 = kind_m(geom, ckW, L, wt, m1);
+        const int kW2 = kind_m(geom, ckW, L, wt, m2), kE0 = kind_m(geom, ckE, L, wt, m0);
+        const int kE1 = kind_m(geom, ckE, L, wt, m1), kE2 = kind_m(geom, ckE, L, wt, m2);
+        if (kA1 != 0)
+          peA0 = ghost_phi(kA1, hk, prB1, kB1, prA0, kA0, wC, kW1, prA2, kA2, prB0, kB0, wN, kW0,
+                           wS, kW2, prB2, kB2);
+        if (kB1 != 0)
+          peB0 = ghost_phi(kB1, hk, eC, kE1, prB0, kB0, prA1, kA1, prB2, kB2, eN, kE0, prA0, kA0,
+                           prA2, kA2, eS, kE2);
       }
-      // ---- collision of row Rc = R-2 into cn / on
+      peW0 = __shfl_up_sync(kFull, peB0, 1);
+      peE0 = __shfl_down_sync(kFull, peA0, 1);
+      if (k < 4) {
+        gr = gr + 1 == RG::DG ? 0 : gr + 1;
+        gw = gw + 1 == RG::DG ? 0 : gw + 1;
+        fr_ = fr_ + 1 == RG::DF ? 0 : fr_ + 1;
+        fw = fw + 1 == RG::DF ? 0 : fw + 1;
+        continue;  // warp-uniform: rows below y0 - 1 do not collide
+      }
+      // ---- collision of row Rc = R-2 (both columns)
       const int Rc = R - 2;
+      const int kA2 = kind_m(geom, ckA, L, wt, m2), kB2 = kind_m(geom, ckB, L, wt, m2);
+      float fsA[9], fsB[9], gPA[4], gPB[4], gSA[4], gSB[4], g0A, g0B;
+      float dg[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       {
-        const float nW = __shfl_up_sync(kFull, pe0, 1), nE = __shfl_down_sync(kFull, pe0, 1);
-        const float cW = __shfl_up_sync(kFull, pe1, 1), cE = __shfl_down_sync(kFull, pe1, 1);
-        const float sW = __shfl_up_sync(kFull, pe2, 1), sE = __shfl_down_sync(kFull, pe2, 1);
-        // diagnostics of this cell: ink weight e, e n, e n u_y, n, phi, n u_y
-        float dg[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        // Every lane runs the collision (no divergent branch, so the
-        // collision and the streaming below form one block the compiler can
-        // interleave); only lanes with a fluid cell that is pulled from
-        // (cvalid) raise the flag or count in the diagnostics.  The results
-        // of the other lanes are never read: a fluid cell pulling from a
-        // solid one takes its own bounce-back value instead.
-        const bool cvalid = col_lane && k2 == 0;
-        if (k >= 4) {
-          int s2 = sl - 2;
-          if (s2 < 0) s2 += D;
-          const float* sg = ring + s2 * kRowW;
-          float g2[5], fr[9];
-#pragma unroll
-          for (int i = 0; i < 5; i++) g2[i] = ring_g(sg, i);
-#pragma unroll
-          for (int i = 0; i < 9; i++) fr[i] = ring_f(sg, i);
-          const float pC = pe1;
-          // lap = 6 sum_i w_i (phi_i - phi) from the differences, which are
-          // exact where neighbours are close (no cancellation of O(10) terms)
-          const float lap = (2.0f / 3.0f) * ((cE - pC) + (pe0 - pC) + (cW - pC) + (pe2 - pC)) +
-                            (1.0f / 6.0f) * ((nE - pC) + (nW - pC) + (sW - pC) + (sE - pC));
-          const float gx = (cE - cW) * (1.0f / 3.0f) + (nE - nW - sW + sE) * (1.0f / 12.0f);
-          const float gy = (pe0 - pe2) * (1.0f / 3.0f) + (nE + nW - sW - sE) * (1.0f / 12.0f);
-          const float phi = pr2;  // sum of g2 in the same order (raw phi of row R-2)
-          const float mu = A4 * phi * ((phi - phis) * (phi + phis)) - kappa * lap;
-          float C = 0.5f * (phi * inv_phis + 1.0f);
-          C = fminf(fmaxf(C, 0.0f), 1.0f);
-          const float Fb = (drive_col && m2 < L) || geom != GEOM_NOZZLE ? Fd * C : 0.0f;
-          const float Fx = mu * gx, Fy = mu * gy + Fb;
-          // fr holds deviations f_i - w_i n0: their sum is n - n0
-          const float dn = fr[0] + fr[1] + fr[2] + fr[3] + fr[4] + fr[5] + fr[6] + fr[7] + fr[8];
-          const float n = n0 + dn;
-          const float mx = fr[1] - fr[3] + fr[5] - fr[6] - fr[7] + fr[8];
-          const float my = fr[2] - fr[4] + fr[5] + fr[6] - fr[7] - fr[8];
-          const float inv_n = __frcp_rn(n);  // 1 / n, correctly rounded
-          const float ux = (mx + 0.5f * Fx) * inv_n, uy = (my + 0.5f * Fy) * inv_n;
-          const float u2 = ux * ux + uy * uy;
-          if (cvalid && !(u2 < 0.09f)) atomicOr(I.status, kStatusNumeric);
-          const float om = __frcp_rn(0.5f + 3.0f * (nu_air + C * dnu));
-          const float pref = 3.0f * (1.0f - 0.5f * om);
-          // A_i - n0 = 3 (phi mu + n / 3) - n0 for i >= 1 (Eq. 6), on deviations
-          const float p3 = dn + 3.0f * phi * mu;
-          const float uF = ux * Fx + uy * Fy;
-          const float base = -1.5f * u2;  // velocity-independent part of the bracket of Eq. 5
-          // Moving directions first (deviations feq_i - w_i n0); the rest
-          // direction then takes the balance, feq_0 - w_0 n0 = (n - n0) -
-          // sum_{i>=1} (feq_i - w_i n0) and F_0 = -sum_{i>=1} F_i.  This equals
-          // A_0 of Eq. 6 (the moments of Eq. 5-6 and of the forcing term are
-          // exact) but conserves mass in FP32, whose rounded weights 4/9,
-          // 1/9, 1/36 do not sum to one.  Opposite directions i, i' share the
-          // even part of the equilibrium and of the forcing term and differ
-          // in the sign of the odd part: feq = E +- O, F = FE +- FO with
-          // E = w (p3 + n (base + 4.5 cu^2)), O = 3 w n cu,
-          // FE = w pref (3 cu cF - uF), FO = w pref cF.  The collision
-          // f* = (1 - om) f + om feq + F then reads f*_i = (1 - om) f_i + A +- B
-          // with A = om E + FE and B = om O + FO.
-          float fs[9];
-          float sumA = 0.0f;
-          const float omc = 1.0f - om, on3 = om * 3.0f * n;
-#pragma unroll
-          for (int i = 1; i < 9; i++) {
-            if (i == 3 || i == 4 || i == 7 || i == 8) continue;  // handled with its pair
-            const int ib = i == 1 ? 3 : (i == 2 ? 4 : (i == 5 ? 7 : 8));
-            const float w = i < 5 ? W1 : W2;
-            const float ex = (float)cEX(i), ey = (float)cEY(i);
-            const float cu = ex * ux + ey * uy;
-            const float cF = ex * Fx + ey * Fy;
-            const float E = w * fmaf(n, fmaf(4.5f * cu, cu, base), p3);
-            const float wp = w * pref;
-            const float FE = wp * fmaf(3.0f * cu, cF, -uF);
-            const float A = fmaf(om, E, FE);
-            const float B = fmaf(w * on3, cu, wp * cF);
-            sumA += A;
-            fs[i] = fmaf(omc, fr[i], A + B);
-            fs[ib] = fmaf(omc, fr[ib], A - B);
+        float ga[5], gb[5], fa[9], fb[9];
+        int s2 = gr - 2;
+        if (s2 < 0) s2 += RG::DG;
+        load_g(s2, ga, gb);
+        load_f(fr_, fa, fb);
+        const bool drv = geom != GEOM_NOZZLE || (m2 >= 0 && m2 < L);
+        float nA, uyA, u2A, nB, uyB, u2B;
+        collide_cell(fa, ga, prA2, peA1, peB1, peA0, peW1, peA2, peB0, peW0, peW2, peB2,
+                     drv && dA, K, fsA, gPA, gSA, g0A, nA, uyA, u2A);
+        collide_cell(fb, gb, prB2, peB1, peE1, peB0, peA1, peB2, peE0, peA0, peA2, peE2,
+                     drv && dB, K, fsB, gPB, gSB, g0B, nB, uyB, u2B);
+        // only fluid cells whose results are used raise the flag or count
+        const bool cA = vA && kA2 == 0, cB = vB && kB2 == 0;
+        if ((cA && !(u2A < 0.09f)) || (cB && !(u2B < 0.09f))) atomicOr(I.status, kStatusNumeric);
+        if (DIAG && Rc >= y0 && Rc < y0 + ch) {
+          const bool oA = cA && wA, oB = cB && wB;
+          const float eA = fminf(fmaxf(prA2 * K.inv_phis, 0.0f), 1.0f);
+          const float eB = fminf(fmaxf(prB2 * K.inv_phis, 0.0f), 1.0f);
+          if (oA) {
+            dg[0] += eA; dg[1] += eA * nA; dg[2] += eA * nA * uyA;
+            dg[3] += nA; dg[4] += prA2; dg[5] += nA * uyA;
           }
-          fs[0] = fmaf(omc, fr[0], fmaf(om, dn, -2.0f * sumA));
-#pragma unroll
-          for (int i = 1; i < 9; i++) cn[i - 1] = fs[i];
-          // order parameter: Eq. 9-10 with the rest direction special; the
-          // moving part q g_i + Omega_i streams, (1 - q) g_i stays
-          const float gmu = gamma * mu;
-          const float pq = phi * inv2q;
-          float sum_ge = 0.0f;
-#pragma unroll
-          for (int i = 1; i < 5; i++) {
-            const float cu = (float)cEX(i) * ux + (float)cEY(i) * uy;
-            const float ge = 0.5f * gmu + pq * cu;
-            sum_ge += ge;
-            cn[7 + i] = fmaf(qmt, g2[i], ge * inv_tphi);  // q g + (ge - g) / tau_phi
-            on[1 + i] = omq * g2[i];
-          }
-          // rest direction: g0_0 = phi - sum_{i>=1} g0_i (Eq. 10 as a
-          // balance, so that sum g0 = phi exactly); with phi - g_0 =
-          // sum_{i>=1} g_i the relaxation uses small terms only
-          on[0] = fs[0];
-          on[1] = g2[0] + ((g2[1] + g2[2] + g2[3] + g2[4]) - sum_ge) * inv_tphi;
-          if (DIAG && cvalid && out_lane && Rc >= y0 && Rc < y0 + ch) {
-            const float e = fminf(fmaxf(phi * inv_phis, 0.0f), 1.0f);
-            dg[0] = e;
-            dg[1] = e * n;
-            dg[2] = dg[1] * uy;
-            dg[3] = n;
-            dg[4] = phi;
-            dg[5] = n * uy;
-          }
-        }
-        if (DIAG && k >= 4 && Rc >= y0 && Rc < y0 + ch) {
-          // the strip's 28 cells of the row are summed in FP32, every
-          // total across strips, rows and chunks in FP64
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-            for (int j = 0; j < 6; j++) dg[j] += __shfl_down_sync(kFull, dg[j], o);
-          if (lane == 0) {
-            atomicAdd(I.rows + Rc, (double)dg[0]);
-            atomicAdd(I.rows + ny + Rc, (double)dg[1]);
-            atomicAdd(I.rows + 2 * ny + Rc, (double)dg[2]);
-            acc_n += (double)dg[3];
-            acc_phi += (double)dg[4];
-            acc_mom += (double)dg[5];
+          if (oB) {
+            dg[0] += eB; dg[1] += eB * nB; dg[2] += eB * nB * uyB;
+            dg[3] += nB; dg[4] += prB2; dg[5] += nB * uyB;
           }
         }
       }
-      // ---- streaming of row Y = R-3: pull f_i(Y) = f*_i(Y - c_i) and
-      // g_i(Y) = (1 - q) g_i(Y) + P_i(Y - c_i); rows Y-1 (cA), Y (cB), Y+1 (cn)
-      {
-        const float w1 = __shfl_up_sync(kFull, cB[0], 1), w5 = __shfl_up_sync(kFull, cA[1], 1);
-        const float w8 = __shfl_up_sync(kFull, cn[7], 1), wP1 = __shfl_up_sync(kFull, cB[8], 1);
-        const float e3 = __shfl_down_sync(kFull, cB[2], 1), e6 = __shfl_down_sync(kFull, cA[2], 1);
-        const float e7 = __shfl_down_sync(kFull, cn[6], 1), eP3 = __shfl_down_sync(kFull, cB[10], 1);
-        const bool svalid = out_lane && k3 == 0;
-        if (k >= 6) {
-          const int Y = R - 3;
-          float fn[9];
-          fn[0] = oB[0];
-          fn[1] = w1;
-          fn[2] = cA[0];
-          fn[3] = e3;
-          fn[4] = cn[3];
-          fn[5] = w5;
-          fn[6] = e6;
-          fn[7] = e7;
-          fn[8] = w8;
-          float P1 = wP1, P2 = cA[3], P3 = eP3, P4 = cn[11];
-          if (svalid && near_solid_v(geom, bc, ny, L, wt, colwall, Y)) {
-            // halfway bounce-back: a population whose source is solid is the
-            // cell's own post-collision population of the opposite direction
-            const unsigned sm = solid_sources(I, x, Y);
-            if (sm) {
-              if (sm & (1u << 1)) { fn[1] = cB[2]; P1 = cB[10]; }
-              if (sm & (1u << 2)) { fn[2] = cB[3]; P2 = cB[11]; }
-              if (sm & (1u << 3)) { fn[3] = cB[0]; P3 = cB[8]; }
-              if (sm & (1u << 4)) { fn[4] = cB[1]; P4 = cB[9]; }
-              if (sm & (1u << 5)) fn[5] = cB[6];
-              if (sm & (1u << 6)) fn[6] = cB[7];
-              if (sm & (1u << 7)) fn[7] = cB[4];
-              if (sm & (1u << 8)) fn[8] = cB[5];
+      if (DIAG && Rc >= y0 && Rc < y0 + ch) {
+        // the strip's cells of the row are summed in FP32, every total
+        // across strips, rows and chunks in FP64
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+          for (int j = 0; j < 6; j++) dg[j] += __shfl_down_sync(kFull, dg[j], o);
+        if (lane == 0) {
+          atomicAdd(I.rows + Rc, (double)dg[0]);
+          atomicAdd(I.rows + ny + Rc, (double)dg[1]);
+          atomicAdd(I.rows + 2 * ny + Rc, (double)dg[2]);
+          acc_n += (double)dg[3];
+          acc_phi += (double)dg[4];
+          acc_mom += (double)dg[5];
+        }
+      }
+      // movers that cross to the neighbouring lane
+      const float sh7 = __shfl_down_sync(kFull, fsA[7], 1);  // f*_7 of B's east neighbour
+      const float sh8 = __shfl_up_sync(kFull, fsB[8], 1);    // f*_8 of A's west neighbour
+      const float sh1 = __shfl_up_sync(kFull, fsB[1], 1), shP1 = __shfl_up_sync(kFull, gPB[0], 1);
+      const float sh3 = __shfl_down_sync(kFull, fsA[3], 1), shP3 = __shfl_down_sync(kFull, gPA[2], 1);
+      const float sh5 = __shfl_up_sync(kFull, fsB[5], 1), sh6 = __shfl_down_sync(kFull, fsA[6], 1);
+      // does any lane have a solid source among rows Rc-1 .. Rc (warp-uniform)
+      const bool solid_rows = __any_sync(
+          kFull, m2 < 0 || m3 < 0 ||
+                     (colmay && ((geom == GEOM_NOZZLE && (m2 < L || m3 < L)) ||
+                                 (geom == GEOM_PLATE && (m2 < wt || m3 < wt)))));
+      // ---- row Y = R-3: downward movers of row Rc, bounce-back, store
+      if (k >= 6) {
+        const int Y = R - 3;
+        float f4A = fsA[4], f7A = fsB[7], f8A = sh8, p4A = gPA[3];
+        float f4B = fsB[4], f7B = sh7, f8B = fsA[8], p4B = gPB[3];
+        const int kA3 = kind_m(geom, ckA, L, wt, m3), kB3 = kind_m(geom, ckB, L, wt, m3);
+        if (solid_rows) {
+          const int kW2 = kind_m(geom, ckW, L, wt, m2), kE2 = kind_m(geom, ckE, L, wt, m2);
+          // sources (x, Y+1), (x+1, Y+1), (x-1, Y+1)
+          if (kA2 != 0) { f4A = upA[0]; p4A = upA[3]; }
+          if (kB2 != 0) { f7A = bbA[0]; }
+          if (kW2 != 0) { f8A = bbA[1]; }
+          if (kB2 != 0) { f4B = upB[0]; p4B = upB[3]; }
+          if (kE2 != 0) { f7B = bbB[0]; }
+          if (kA2 != 0) { f8B = bbB[1]; }
+        }
+        const bool sA = wA && kA3 == 0, sB = wB && kB3 == 0;
+        const float fA[9] = {aA[0], aA[1], aA[2], aA[3], f4A, aA[4], aA[5], f7A, f8A};
+        const float fB[9] = {aB[0], aB[1], aB[2], aB[3], f4B, aB[4], aB[5], f7B, f8B};
+        const float gA[5] = {aA[6], aA[7], aA[8], aA[9], aA[10] + p4A};
+        const float gB[5] = {aB[6], aB[7], aB[8], aB[9], aB[10] + p4B};
+        const int cA = Y * nx + xA, cB = Y * nx + xB;
+        if (!ODD && sA && sB) {
+          if (!H) {
+#pragma unroll
+            for (int i = 0; i < 9; i++)
+              *reinterpret_cast<float2*>(fout + (size_t)i * N + cA) = make_float2(fA[i], fB[i]);
+#pragma unroll
+            for (int i = 0; i < 5; i++)
+              *reinterpret_cast<float2*>(gout + (size_t)i * N + cA) = make_float2(gA[i], gB[i]);
+          } else {
+            // round to nearest even on store
+#pragma unroll
+            for (int i = 0; i < 9; i++)
+              *reinterpret_cast<__half2*>(fhout + (size_t)i * N + cA) = __floats2half2_rn(fA[i], fB[i]);
+            *reinterpret_cast<float2*>(gout + cA) = make_float2(gA[0], gB[0]);
+#pragma unroll
+            for (int i = 1; i < 5; i++)
+              *reinterpret_cast<__half2*>(ghout + (size_t)(i - 1) * N + cA) =
+                  __floats2half2_rn(gA[i], gB[i]);
+          }
+        } else {
+          if (!H) {
+            if (sA) {
+#pragma unroll
+              for (int i = 0; i < 9; i++) fout[(size_t)i * N + cA] = fA[i];
+#pragma unroll
+              for (int i = 0; i < 5; i++) gout[(size_t)i * N + cA] = gA[i];
+            }
+            if (sB) {
+#pragma unroll
+              for (int i = 0; i < 9; i++) fout[(size_t)i * N + cB] = fB[i];
+#pragma unroll
+              for (int i = 0; i < 5; i++) gout[(size_t)i * N + cB] = gB[i];
+            }
+          } else {
+            if (sA) {
+#pragma unroll
+              for (int i = 0; i < 9; i++) fhout[(size_t)i * N + cA] = __float2half_rn(fA[i]);
+              gout[cA] = gA[0];
+#pragma unroll
+              for (int i = 1; i < 5; i++) ghout[(size_t)(i - 1) * N + cA] = __float2half_rn(gA[i]);
+            }
+            if (sB) {
+#pragma unroll
+              for (int i = 0; i < 9; i++) fhout[(size_t)i * N + cB] = __float2half_rn(fB[i]);
+              gout[cB] = gB[0];
+#pragma unroll
+              for (int i = 1; i < 5; i++) ghout[(size_t)(i - 1) * N + cB] = __float2half_rn(gB[i]);
             }
           }
-          if (svalid && !H) {
-            float* fo = fout + Y * nx + x;
-            float* go = gout + Y * nx + x;
-#pragma unroll
-            for (int i = 0; i < 9; i++) fo[i * N] = fn[i];
-            go[0] = oB[1];
-            go[N] = oB[2] + P1;
-            go[2 * N] = oB[3] + P2;
-            go[3 * N] = oB[4] + P3;
-            go[4 * N] = oB[5] + P4;
-          } else if (svalid) {
-            // round to nearest even on store
-            __half* fo = fhout + Y * nx + x;
-            __half* go = ghout + Y * nx + x;
-#pragma unroll
-            for (int i = 0; i < 9; i++) fo[i * N] = __float2half_rn(fn[i]);
-            gout[Y * nx + x] = oB[1];
-            go[0] = __float2half_rn(oB[2] + P1);
-            go[N] = __float2half_rn(oB[3] + P2);
-            go[2 * N] = __float2half_rn(oB[4] + P3);
-            go[3 * N] = __float2half_rn(oB[5] + P4);
-          }
         }
       }
-      cA[0] = cB[1];  // f*_2
-      cA[1] = cB[4];  // f*_5
-      cA[2] = cB[5];  // f*_6
-      cA[3] = cB[9];  // P_2
-#pragma unroll
-      for (int i = 0; i < 12; i++) cB[i] = cn[i];
-#pragma unroll
-      for (int i = 0; i < 6; i++) oB[i] = on[i];
-      sl = sl + 1 == D ? 0 : sl + 1;
+      // ---- gather the pulls of row Rc (rest, sideways, upward movers of
+      // row Rc-1, stay parts) into aA / aB; keep the upward movers of row Rc
+      {
+        // f_0, f_1 (from x-1), f_2 (from x, Rc-1), f_3 (from x+1),
+        // f_5 (from x-1, Rc-1), f_6 (from x+1, Rc-1); g_0 .. g_4
+        float f1A = sh1, f3A = fsB[3], f2A = upA[0], f5A = upA[1], f6A = upA[2];
+        float p1A = shP1, p3A = gPB[2], p2A = upA[3];
+        float f1B = fsA[1], f3B = sh3, f2B = upB[0], f5B = upB[1], f6B = upB[2];
+        float p1B = gPA[0], p3B = shP3, p2B = upB[3];
+        if (solid_rows) {
+          const int kW2 = kind_m(geom, ckW, L, wt, m2), kE2 = kind_m(geom, ckE, L, wt, m2);
+          const int kA3 = kind_m(geom, ckA, L, wt, m3), kB3 = kind_m(geom, ckB, L, wt, m3);
+          const int kW3 = kind_m(geom, ckW, L, wt, m3), kE3 = kind_m(geom, ckE, L, wt, m3);
+          // A: sources (x-1, Rc) = W, (x+1, Rc) = B, (x, Rc-1) = A,
+          // (x-1, Rc-1) = W, (x+1, Rc-1) = B
+          if (kW2 != 0) { f1A = fsA[3]; p1A = gPA[2]; }
+          if (kB2 != 0) { f3A = fsA[1]; p3A = gPA[0]; }
+          if (kA3 != 0) { f2A = fsA[4]; p2A = gPA[3]; }
+          if (kW3 != 0) f5A = fsA[7];
+          if (kB3 != 0) f6A = fsA[8];
+          // B: (x-1, Rc) = A, (x+1, Rc) = E, (x, Rc-1) = B, (x-1, Rc-1) = A,
+          // (x+1, Rc-1) = E
+          if (kA2 != 0) { f1B = fsB[3]; p1B = gPB[2]; }
+          if (kE2 != 0) { f3B = fsB[1]; p3B = gPB[0]; }
+          if (kB3 != 0) { f2B = fsB[4]; p2B = gPB[3]; }
+          if (kA3 != 0) f5B = fsB[7];
+          if (kE3 != 0) f6B = fsB[8];
+        }
+        aA[0] = fsA[0]; aA[1] = f1A; aA[2] = f2A; aA[3] = f3A; aA[4] = f5A; aA[5] = f6A;
+        aA[6] = g0A; aA[7] = gSA[0] + p1A; aA[8] = gSA[1] + p2A; aA[9] = gSA[2] + p3A;
+        aA[10] = gSA[3];
+        aB[0] = fsB[0]; aB[1] = f1B; aB[2] = f2B; aB[3] = f3B; aB[4] = f5B; aB[5] = f6B;
+        aB[6] = g0B; aB[7] = gSB[0] + p1B; aB[8] = gSB[1] + p2B; aB[9] = gSB[2] + p3B;
+        aB[10] = gSB[3];
+        upA[0] = fsA[2]; upA[1] = sh5; upA[2] = fsB[6]; upA[3] = gPA[1];
+        upB[0] = fsB[2]; upB[1] = fsA[5]; upB[2] = sh6; upB[3] = gPB[1];
+        bbA[0] = fsA[5]; bbA[1] = fsA[6];
+        bbB[0] = fsB[5]; bbB[1] = fsB[6];
+      }
+      gr = gr + 1 == RG::DG ? 0 : gr + 1;
+      gw = gw + 1 == RG::DG ? 0 : gw + 1;
+      fr_ = fr_ + 1 == RG::DF ? 0 : fr_ + 1;
+      fw = fw + 1 == RG::DF ? 0 : fw + 1;
     }
     cp_async_wait<0>();  // no copy may land after the warp moves on
     if (DIAG && lane == 0) {
@@ -1004,7 +1116,9 @@ __global__ void f_convert_kernel(const Inst* __restrict__ insts, int index, cons
 
 // ---------------------------------------------------------------------------
 size_t step_smem_bytes(int nthreads, int prefetch, bool h16) {
-  return (size_t)(nthreads / 32) * (prefetch + 3) * (h16 ? kRowWordsH : kRowFloats) * sizeof(float);
+  // per warp: g ring (P+3 rows) with the edge lanes' outer column, f ring (P+1 rows)
+  const int gw = h16 ? 192 : 320, fw = h16 ? 288 : 576, ow = 20;
+  return (size_t)(nthreads / 32) * ((prefetch + 3) * (gw + ow) + (prefetch + 1) * fw) * sizeof(float);
 }
 
 size_t state_bytes_f(const Inst& I) { return (size_t)I.nx * I.ny * 9 * (I.fp16 ? 2 : 4); }
@@ -1061,22 +1175,22 @@ cudaError_t launch_convert16(const Inst* d_inst, const Inst& h, int index, int p
   return cudaGetLastError();
 }
 
-template <bool DIAG, bool H>
-cudaError_t launch_step_p(const Inst* d_inst, const Item* d_items, int n_items, int nthreads,
-                          int grid, const long long* d_t, int t_off, int prefetch, size_t smem,
+template <bool DIAG, bool H, bool ODD>
+cudaError_t launch_step_p(const Inst* d_inst, const Item* d_items, int n_items, int grid,
+                          const long long* d_t, int t_off, int prefetch, size_t smem,
                           cudaStream_t s) {
   switch (prefetch) {
     case 1:
-      step_kernel<DIAG, 1, H><<<grid, nthreads, smem, s>>>(d_inst, d_items, n_items, d_t, t_off);
+      step_kernel<DIAG, 1, H, ODD><<<grid, 32, smem, s>>>(d_inst, d_items, n_items, d_t, t_off);
       break;
     case 2:
-      step_kernel<DIAG, 2, H><<<grid, nthreads, smem, s>>>(d_inst, d_items, n_items, d_t, t_off);
+      step_kernel<DIAG, 2, H, ODD><<<grid, 32, smem, s>>>(d_inst, d_items, n_items, d_t, t_off);
       break;
     case 3:
-      step_kernel<DIAG, 3, H><<<grid, nthreads, smem, s>>>(d_inst, d_items, n_items, d_t, t_off);
+      step_kernel<DIAG, 3, H, ODD><<<grid, 32, smem, s>>>(d_inst, d_items, n_items, d_t, t_off);
       break;
     default:
-      step_kernel<DIAG, 4, H><<<grid, nthreads, smem, s>>>(d_inst, d_items, n_items, d_t, t_off);
+      step_kernel<DIAG, 4, H, ODD><<<grid, 32, smem, s>>>(d_inst, d_items, n_items, d_t, t_off);
       break;
   }
   return cudaGetLastError();
@@ -1084,42 +1198,40 @@ cudaError_t launch_step_p(const Inst* d_inst, const Item* d_items, int n_items, 
 
 cudaError_t launch_step(const Inst* d_inst, const Item* d_items, int n_items, int nthreads,
                         int grid, const long long* d_t, int t_off, bool diag, int prefetch,
-                        bool h16, cudaStream_t s) {
-  if (nthreads != kStepThreads || prefetch < 1 || prefetch > kMaxPrefetch)
+                        bool h16, bool odd, cudaStream_t s) {
+  if (nthreads != kStepThreads || prefetch < 1 || prefetch > kMaxPrefetch || (h16 && odd))
     return cudaErrorInvalidValue;
   if (n_items <= 0) return cudaSuccess;
   const size_t smem = step_smem_bytes(nthreads, prefetch, h16);
-  if (h16)
-    return diag ? launch_step_p<true, true>(d_inst, d_items, n_items, nthreads, grid, d_t, t_off,
-                                            prefetch, smem, s)
-                : launch_step_p<false, true>(d_inst, d_items, n_items, nthreads, grid, d_t, t_off,
-                                             prefetch, smem, s);
-  return diag ? launch_step_p<true, false>(d_inst, d_items, n_items, nthreads, grid, d_t, t_off,
-                                           prefetch, smem, s)
-              : launch_step_p<false, false>(d_inst, d_items, n_items, nthreads, grid, d_t, t_off,
-                                            prefetch, smem, s);
+#define LAUNCH_STEP(DG, HH, OD) \
+  launch_step_p<DG, HH, OD>(d_inst, d_items, n_items, grid, d_t, t_off, prefetch, smem, s)
+  if (h16) return diag ? LAUNCH_STEP(true, true, false) : LAUNCH_STEP(false, true, false);
+  if (odd) return diag ? LAUNCH_STEP(true, false, true) : LAUNCH_STEP(false, false, true);
+  return diag ? LAUNCH_STEP(true, false, false) : LAUNCH_STEP(false, false, false);
+#undef LAUNCH_STEP
 }
 
-int step_prefetch_for(int) { return 3; }
+int step_prefetch_for(int) { return 2; }
 
 cudaError_t set_step_smem_limit() {
   const int lim = (int)step_smem_bytes(kStepThreads, kMaxPrefetch, false);
   cudaError_t e = cudaSuccess;
-#define SET_LIM(DG, PF)                                                                         \
-  if (e == cudaSuccess)                                                                         \
-    e = cudaFuncSetAttribute(step_kernel<DG, PF, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                             lim);                                                              \
-  if (e == cudaSuccess)                                                                         \
-    e = cudaFuncSetAttribute(step_kernel<DG, PF, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                             lim);
-  SET_LIM(true, 1) SET_LIM(false, 1) SET_LIM(true, 2) SET_LIM(false, 2)
-  SET_LIM(true, 3) SET_LIM(false, 3) SET_LIM(true, 4) SET_LIM(false, 4)
+#define SET_LIM(DG, PF, HH, OD)                                                               \
+  if (e == cudaSuccess)                                                                       \
+    e = cudaFuncSetAttribute(step_kernel<DG, PF, HH, OD>,                                     \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+#define SET_LIM_P(PF) \
+  SET_LIM(true, PF, false, false) SET_LIM(false, PF, false, false) \
+  SET_LIM(true, PF, true, false) SET_LIM(false, PF, true, false)   \
+  SET_LIM(true, PF, false, true) SET_LIM(false, PF, false, true)
+  SET_LIM_P(1) SET_LIM_P(2) SET_LIM_P(3) SET_LIM_P(4)
+#undef SET_LIM_P
 #undef SET_LIM
   return e;
 }
 
 int make_items_range(const Inst& I, int k, int chunk, int ya, int yb, Item* out, int cap) {
-  constexpr int halo = 2, W = 32 - 2 * halo;  // 28 written columns per strip
+  constexpr int halo = 2, W = kStripCols;  // 60 written columns per strip (2 per lane)
   const int nstrip = (I.nx + W - 1) / W;
   int n = 0;
   for (int y0 = ya; y0 < yb; y0 += chunk)
@@ -1141,7 +1253,7 @@ int make_items(const Inst& I, int k, int chunk, Item* out, int cap) {
 }
 
 int items_per_range(const Inst& I, int chunk, int ya, int yb) {
-  return yb > ya ? ((I.nx + 27) / 28) * ((yb - ya + chunk - 1) / chunk) : 0;
+  return yb > ya ? ((I.nx + kStripCols - 1) / kStripCols) * ((yb - ya + chunk - 1) / chunk) : 0;
 }
 
 int items_per_lattice(const Inst& I, int chunk) { return items_per_range(I, chunk, 0, I.ny); }

@@ -107,11 +107,12 @@ def test_ragged_and_degenerate_sizes_fp16(ij, nx, ny):
     _fp16_step_case(ij, p)
 
 
-@pytest.mark.parametrize("cx", [26, 27, 28, 29, 30])
+@pytest.mark.parametrize("cx", [58, 59, 60, 61, 62, 63])
 def test_wall_on_strip_edges_fp16(ij, cx):
-    """Nozzle walls whose wetting faces fall on the edge lanes of a strip
-    (lanes 0 / 31 stage the g of the column outside the strip)."""
-    nx = 84
+    """Nozzle walls across the edges of the 60-column strips (nx = 180: the
+    walls cross columns 60 and 120); at cx = 62 lanes 0 / 31 stage the g of
+    the column outside the strip."""
+    nx = 180
     width = nx - 2 * cx
     p = W.small_nozzle(nx=nx, ny=40, nozzle_width=width, nozzle_length=20, wall_thickness=4)
     _fp16_step_case(ij, p)

@@ -102,11 +102,27 @@ def test_ragged_and_degenerate_sizes(ij, nx, ny):
     _one_step_case(ij, p, steps=3, tol=1e-5)
 
 
-@pytest.mark.parametrize("cx", [26, 27, 28, 29, 30])
+@pytest.mark.parametrize("cx", [57, 58, 59, 60, 61, 62, 63, 64])
 def test_wall_on_strip_edges(ij, cx):
-    """Nozzle walls on the edge lanes of the 28-column strips (at cx = 30
-    all four edge-lane cases: wall column inside the strip, fluid outside)."""
-    nx = 84
+    """Nozzle walls across the edges of the 60-column strips: nx = 180 puts
+    the left wall [cx-4, cx) across column 60 and the right wall
+    [180-cx, 184-cx) across column 120.  Every case of the edge columns
+    (the two halo columns each side of a strip, held by lanes 0 and 31)
+    occurs: fluid or wall, the wetting face on or beside them, and a solid
+    halo column whose neighbour outside the strip is fluid (cx = 62: the
+    lanes stage the g of the column outside)."""
+    nx = 180
+    p = W.small_nozzle(nx=nx, ny=40, nozzle_width=nx - 2 * cx, nozzle_length=20,
+                       wall_thickness=4)
+    _one_step_case(ij, p, steps=3, tol=1e-5)
+
+
+@pytest.mark.parametrize("cx", [59, 60, 61, 62, 63])
+def test_wall_on_strip_edges_odd_width(ij, cx):
+    """The same on an odd-width lattice (nx = 181: column pairs are copied
+    one column at a time), where the strips start at odd and even
+    addresses."""
+    nx = 181
     p = W.small_nozzle(nx=nx, ny=40, nozzle_width=nx - 2 * cx, nozzle_length=20,
                        wall_thickness=4)
     _one_step_case(ij, p, steps=3, tol=1e-5)
