@@ -205,20 +205,29 @@ ij_status ij_kernel_timing(ij_handle h, int enable, double* total_ms, long long*
 /*
  * Launch-shape tuning (no counterpart in the paper).  The step kernel runs
  * one warp per work item: a strip of 60 columns, two per lane (plus two halo
- * columns on each side), times a chunk of `chunk` rows of one lattice, with
- * the populations staged `prefetch` rows (1..4) ahead of use; every block is
+ * columns on each side), times a range of rows of one lattice, with the
+ * populations staged `prefetch` rows (1..4) ahead of use; every block is
  * one warp (32 threads), so a finished item frees its slot at once.  Every
  * lattice of a handle is in the one bucket of 32-thread blocks.  The work
- * list starts with the rows of nozzle-wall strips below the nozzle exit
- * (costlier per row) and ends with the last eighth of each lattice's rows,
- * both in chunks a quarter as long, so that the SMs finish together.
+ * list comes in two forms, chosen by `chunk`:
+ *   chunk >= 1 : rows cut into chunks of `chunk` rows; the list starts with
+ *                the rows of nozzle-wall strips below the nozzle exit
+ *                (costlier per row) and ends with the last eighth of each
+ *                lattice's rows, both in chunks a quarter as long;
+ *   chunk <= 0 : cost-balanced (the default, 0): with S the number of items
+ *                the GPU runs at once, each strip's first rows -- 7/8 of its
+ *                cost, wall rows counting 2.2 -- are cut into pieces of
+ *                equal cost near one S-th of the total (one wave that ends
+ *                together), the rest into short pieces listed last; -1: the
+ *                whole strip in equal pieces, no tail; -2: 3/4 and a tail of
+ *                shorter pieces.
  *
- * ij_tune      -- set chunk and prefetch (block_size: 32, or <= 0 for
- *                 every bucket).  Synchronises.
+ * ij_tune      -- set chunk (>= -2) and prefetch (block_size: 32, or <= 0
+ *                 for every bucket).  Synchronises.
  * ij_autotune  -- time `reps` trial launches of every candidate (chunks
- *                 8..256, prefetch 1..4) on the current state and keep the
- *                 fastest.  Trial launches leave the state and the time
- *                 unchanged.  Synchronises.
+ *                 8..256 and 0, -1, -2; prefetch 1..4) on the current state
+ *                 and keep the fastest.  Trial launches leave the state and
+ *                 the time unchanged.  Synchronises.
  * ij_get_tuning -- block size, chunk, prefetch and item count of bucket
  *                 `bucket` (0-based); IJ_ERR_PARAM past the last bucket.
  * 3-D handles have one fixed launch shape and no buckets: ij_tune returns
@@ -250,8 +259,8 @@ ij_status ij_get_tuning(ij_handle h, int bucket, int* block_size, int* chunk, in
  *                   f_i - w_i n0 on fluid cells (n0 = (rho_ink + rho_air)/2,
  *                   w = 4/9, 1/9, 1/36) and 0 on solid cells; g holds g_i.
  *                   Same [i][y][x] order as above.  Read only.
- *   f_out, g_out  : device, receive the state at t+1 (solid cells untouched);
- *                   must not alias the inputs.
+ *   f_out, g_out  : device, receive the state at t+1 in the same layout (solid
+ *                   cells 0); must not alias the inputs.
  *   record_out    : device, 13 doubles (ij_obs order) receiving the
  *                   diagnostics record of the state at t, or NULL for none.
  *                   Each call starts a fresh breakup history, so breakup_step

@@ -318,60 +318,165 @@ Inst3 derive3(const ij_params& p) {
 // warp per work item).
 int block_size_for(const Inst&) { return kStepThreads; }
 
+// Rows of one strip that run the wall paths (wetting ghosts, bounce-back):
+// rows below the first row whose stencil no longer reaches a solid cell.
+int strip_wall_rows(const Inst& I, const Item& it) {
+  const int x0 = it.xs - it.halo, x1 = it.xs + it.nout + it.halo;  // columns held
+  if (I.geom == GEOM_NOZZLE) {
+    // either wall band [cx0 - wt, cx0) or [cx1, cx1 + wt) among them (or a
+    // wrapped copy of it)
+    for (int sh = -I.nx; sh <= I.nx; sh += I.nx) {
+      const int a = x0 + sh, b = x1 + sh;
+      if ((b > I.cx0 - I.wt && a < I.cx0) || (b > I.cx1 && a < I.cx1 + I.wt))
+        return std::min(I.ny, I.L + 2);
+    }
+    return 0;
+  }
+  if (I.geom == GEOM_PLATE) return std::min(I.ny, I.wt + 2);
+  return 0;
+}
+
+// Cost-balanced work list (chunk <= 0).  The cost of a strip row is 1, or
+// 1 + kWallCost for a row that runs the wall paths (measured: a wall-strip
+// row takes 2.0-2.2 times a fluid one).  With S the number of work items the
+// GPU runs at once (SMs x resident blocks), the body of every strip -- a
+// fraction beta of its cost, from its first row -- is cut into pieces of
+// equal cost near beta C / S (C the total cost), S pieces in all, so that the
+// body is one wave of items that finish together; the rest of each strip
+// becomes a tail of short pieces listed after all bodies, which the SMs
+// that finish first take up.  Variants: chunk 0 (beta 7/8, tail pieces of a
+// sixth of a body piece), -1 (beta 1, no tail), -2 (beta 3/4, tail pieces of
+// an eighth).
+constexpr double kWallCost = 1.2;
+
+void balanced_items(ij_handle h, const Bucket& b, int slots) {
+  const int variant = -b.chunk;
+  const double beta = variant == 1 ? 1.0 : (variant == 2 ? 0.75 : 0.875);
+  const double tail_div = variant == 2 ? 8.0 : 6.0;
+  struct Strip { Item it; int wall; double cost; };
+  std::vector<Strip> strips;
+  double C = 0.0;
+  for (int k = 0; k < h->n_inst; k++) {
+    const Inst& I = h->inst[k];
+    const int n = items_per_range(I, I.ny, 0, I.ny);
+    const size_t at = h->items.size();
+    h->items.resize(at + n);
+    make_items_range(I, k, I.ny, 0, I.ny, h->items.data() + at, n);
+    for (int j = 0; j < n; j++) {
+      Strip st;
+      st.it = h->items[at + j];
+      st.wall = strip_wall_rows(I, st.it);
+      st.cost = I.ny + kWallCost * st.wall;
+      C += st.cost;
+      strips.push_back(st);
+    }
+    h->items.resize(at);
+  }
+  const double T = beta * C / std::max(1, slots);  // body piece cost
+  // pieces per strip body, summing to exactly `slots` (largest remainders
+  // get the extra pieces; at least one per strip): one more item than the
+  // GPU holds would wait for a whole piece and double the step
+  std::vector<int> nb(strips.size());
+  std::vector<std::pair<double, size_t>> rem;
+  long long total = 0;
+  for (size_t i = 0; i < strips.size(); i++) {
+    const double raw = strips[i].cost * slots / C;
+    nb[i] = std::max(1, (int)floor(raw));
+    total += nb[i];
+    rem.push_back({raw - floor(raw), i});
+  }
+  std::sort(rem.begin(), rem.end(), [](const std::pair<double, size_t>& a,
+                                       const std::pair<double, size_t>& b) { return a.first > b.first; });
+  for (size_t j = 0; j < rem.size() && total < slots; j++, total++) nb[rem[j].second]++;
+  // row at which the cumulative cost of a strip reaches c
+  auto row_at = [](const Strip& st, double c) -> int {
+    const double cw = (1.0 + kWallCost) * st.wall;
+    const double y = c <= cw ? c / (1.0 + kWallCost) : st.wall + (c - cw);
+    return std::max(0, std::min(st.it.ch, (int)lround(y)));
+  };
+  std::vector<Item> tail;
+  for (size_t i = 0; i < strips.size(); i++) {
+    const Strip& st = strips[i];
+    const double body = beta * st.cost;
+    const int yb = beta >= 1.0 ? st.it.ch : std::max(1, row_at(st, body));
+    int y = 0;
+    for (int j = 1; j <= nb[i] && y < yb; j++) {
+      const int ye = j == nb[i] ? yb : std::min(yb, std::max(y + 1, row_at(st, body * j / nb[i])));
+      Item it = st.it;
+      it.y0 = y;
+      it.ch = ye - y;
+      h->items.push_back(it);
+      y = ye;
+    }
+    const int tn = std::max(4, (int)lround(T / tail_div));  // rows per tail piece
+    for (; y < st.it.ch; y += tn) {
+      Item it = st.it;
+      it.y0 = y;
+      it.ch = std::min(tn, st.it.ch - y);
+      tail.push_back(it);
+    }
+  }
+  h->items.insert(h->items.end(), tail.begin(), tail.end());
+}
+
 void build_items(ij_handle h) {
   std::vector<Bucket> old = h->buckets;
   h->items.clear();
   h->buckets.clear();
-  Bucket b{kStepThreads, 0, 0, 0, 64, step_prefetch_for(kStepThreads)};
+  Bucket b{kStepThreads, 0, 0, 0, 0, step_prefetch_for(kStepThreads)};
   for (const Bucket& o : old)
     if (o.nthreads == kStepThreads) {
       b.chunk = o.chunk;
       b.prefetch = o.prefetch;
     }
-  // The last eighth of every lattice's rows is cut into chunks a quarter as
-  // long, and those items go last: the final wave of blocks is made of short
-  // items, so SMs run out of work together.
-  const int tail_chunk = std::max(4, b.chunk / 4);
-  size_t n_body = 0;  // items before the tail
-  for (int pass = 0; pass < 2; pass++) {
-    if (pass == 1) n_body = h->items.size();
-    for (int k = 0; k < h->n_inst; k++) {
-      const Inst& I = h->inst[k];
-      const int split = I.ny - I.ny / 8;
-      const int ya = pass == 0 ? 0 : split, yb = pass == 0 ? split : I.ny;
-      const int ch = pass == 0 ? b.chunk : tail_chunk;
-      const int n = items_per_range(I, ch, ya, yb);
-      const size_t at = h->items.size();
-      h->items.resize(at + n);
-      make_items_range(I, k, ch, ya, yb, h->items.data() + at, n);
-    }
-  }
-  // Items of nozzle-wall strips below the nozzle exit cost more per row
-  // (wetting ghosts, bounce-back): they go first, cut into chunks a quarter
-  // as long, so that no SM is left with a long one of them at the end.
-  auto costly = [&](const Item& it) {
-    const Inst& I = h->inst[it.inst];
-    if (I.geom != GEOM_NOZZLE || it.y0 > I.L + 1) return false;
-    const int x0 = it.xs - it.halo, x1 = it.xs + it.nout + it.halo;  // columns held
-    // either wall band [cx0 - wt, cx0) or [cx1, cx1 + wt) among them
-    return (x1 > I.cx0 - I.wt && x0 < I.cx0) || (x1 > I.cx1 && x0 < I.cx1 + I.wt);
-  };
-  const size_t n_costly =
-      std::stable_partition(h->items.begin(), h->items.begin() + n_body, costly) -
-      h->items.begin();
-  if (n_costly > 0) {
-    std::vector<Item> split;
-    for (size_t i = 0; i < n_costly; i++) {
-      const Item& it = h->items[i];
-      for (int y = it.y0; y < it.y0 + it.ch; y += tail_chunk) {
-        Item c = it;
-        c.y0 = y;
-        c.ch = std::min(tail_chunk, it.y0 + it.ch - y);
-        split.push_back(c);
+  if (b.chunk <= 0) {
+    balanced_items(h, b, step_slots(b.prefetch, h->fp16, h->odd));
+  } else {
+    // The last eighth of every lattice's rows is cut into chunks a quarter as
+    // long, and those items go last: the final wave of blocks is made of short
+    // items, so SMs run out of work together.
+    const int tail_chunk = std::max(4, b.chunk / 4);
+    size_t n_body = 0;  // items before the tail
+    for (int pass = 0; pass < 2; pass++) {
+      if (pass == 1) n_body = h->items.size();
+      for (int k = 0; k < h->n_inst; k++) {
+        const Inst& I = h->inst[k];
+        const int split = I.ny - I.ny / 8;
+        const int ya = pass == 0 ? 0 : split, yb = pass == 0 ? split : I.ny;
+        const int ch = pass == 0 ? b.chunk : tail_chunk;
+        const int n = items_per_range(I, ch, ya, yb);
+        const size_t at = h->items.size();
+        h->items.resize(at + n);
+        make_items_range(I, k, ch, ya, yb, h->items.data() + at, n);
       }
     }
-    split.insert(split.end(), h->items.begin() + n_costly, h->items.end());
-    h->items.swap(split);
+    // Items of nozzle-wall strips below the nozzle exit cost more per row
+    // (wetting ghosts, bounce-back): they go first, cut into chunks a quarter
+    // as long, so that no SM is left with a long one of them at the end.
+    auto costly = [&](const Item& it) {
+      const Inst& I = h->inst[it.inst];
+      if (I.geom != GEOM_NOZZLE || it.y0 > I.L + 1) return false;
+      const int x0 = it.xs - it.halo, x1 = it.xs + it.nout + it.halo;  // columns held
+      // either wall band [cx0 - wt, cx0) or [cx1, cx1 + wt) among them
+      return (x1 > I.cx0 - I.wt && x0 < I.cx0) || (x1 > I.cx1 && x0 < I.cx1 + I.wt);
+    };
+    const size_t n_costly =
+        std::stable_partition(h->items.begin(), h->items.begin() + n_body, costly) -
+        h->items.begin();
+    if (n_costly > 0) {
+      std::vector<Item> split;
+      for (size_t i = 0; i < n_costly; i++) {
+        const Item& it = h->items[i];
+        for (int y = it.y0; y < it.y0 + it.ch; y += tail_chunk) {
+          Item c = it;
+          c.y0 = y;
+          c.ch = std::min(tail_chunk, it.y0 + it.ch - y);
+          split.push_back(c);
+        }
+      }
+      split.insert(split.end(), h->items.begin() + n_costly, h->items.end());
+      h->items.swap(split);
+    }
   }
   b.count = (int)h->items.size();
   // one block per item: the block scheduler hands new blocks to SMs as
@@ -989,8 +1094,8 @@ ij_status ij_tune(ij_handle h, int block_size, int chunk, int prefetch) {
   ij_status st = check_handle(h);
   if (st != IJ_OK) return st;
   if (h->is3d) return fail(IJ_ERR_PARAM, "3-D handles have no launch shape to tune");
-  if (chunk < 1 || prefetch < 1 || prefetch > kMaxPrefetch)
-    return fail(IJ_ERR_PARAM, "chunk must be >= 1 and prefetch in 1..%d", kMaxPrefetch);
+  if (chunk < -2 || prefetch < 1 || prefetch > kMaxPrefetch)
+    return fail(IJ_ERR_PARAM, "chunk must be >= -2 and prefetch in 1..%d", kMaxPrefetch);
   bool found = false;
   for (Bucket& b : h->buckets)
     if (block_size <= 0 || b.nthreads == block_size) {
@@ -1013,7 +1118,8 @@ ij_status ij_autotune(ij_handle h, int reps) {
   if (reps < 1) return fail(IJ_ERR_PARAM, "reps must be >= 1");
   if (h->poisoned) return fail(IJ_ERR_STATE, "handle is poisoned");
   if (h->is3d) return IJ_OK;  // the 3-D kernels have one fixed launch shape
-  static const int kChunks[] = {8, 16, 24, 32, 48, 64, 96, 128, 256};
+  // row chunks, then the cost-balanced variants (chunk <= 0)
+  static const int kChunks[] = {8, 16, 24, 32, 48, 64, 96, 128, 256, 0, -1, -2};
   cudaEvent_t e0, e1;
   CUDA_TRY(cudaEventCreate(&e0));
   CUDA_TRY(cudaEventCreate(&e1));
@@ -1028,7 +1134,7 @@ ij_status ij_autotune(ij_handle h, int reps) {
     int best_chunk = h->buckets[bi].chunk, best_pf = h->buckets[bi].prefetch;
     for (int pf = 1; pf <= kMaxPrefetch; pf++)
       for (int chunk : kChunks) {
-        if (chunk > 2 * max_ny && chunk != kChunks[0]) continue;
+        if (chunk > 2 * max_ny && chunk > 0) continue;
         h->buckets[bi].chunk = chunk;
         h->buckets[bi].prefetch = pf;
         build_items(h);

@@ -83,6 +83,9 @@ cudaError_t launch_step(const Inst* d_inst, const Item* d_items, int n_items, in
                         bool h16, bool odd, cudaStream_t s);
 // default number of rows staged ahead of use
 int step_prefetch_for(int nthreads);
+// work items the GPU runs at once: SMs x resident blocks of the step kernel
+// (launch without diagnostics) at this prefetch and storage
+int step_slots(int prefetch, bool h16, bool odd);
 cudaError_t launch_finalize(const Inst* d_inst, int n_inst, const long long* d_t,
                             cudaStream_t s);
 cudaError_t launch_advance(long long* d_t, int by, cudaStream_t s);

@@ -162,11 +162,6 @@ __device__ __forceinline__ int row_kind(int geom, int colk, int L, int wt, int y
   if (geom == GEOM_PLATE) return ym < wt ? (ym == wt - 1 ? 2 : 1) : 0;
   return 0;
 }
-// The same for a mapped row m (-1: outside a closed domain, a non-wetting solid).
-__device__ __forceinline__ int kind_m(int geom, int colk, int L, int wt, int m) {
-  return m < 0 ? 1 : row_kind(geom, colk, L, wt, m);
-}
-
 __device__ __forceinline__ int column_kind(const Inst& I, int x) {
   if (I.geom != GEOM_NOZZLE) return 0;
   if ((x >= I.cx0 - I.wt && x < I.cx0) || (x >= I.cx1 && x < I.cx1 + I.wt))
@@ -196,7 +191,18 @@ __device__ __forceinline__ float ghost_phi(int k, float hk, float pE, int kE, fl
     if (kSW == 0) { sum += pSW; cnt++; }
     if (kSE == 0) { sum += pSE; cnt++; }
   }
-  return cnt ? sum / (float)cnt : 0.0f;
+  // the mean: a product with 1 / cnt (within one rounding of sum / cnt)
+  return cnt == 1 ? sum : (cnt == 2 ? 0.5f * sum : (cnt == 3 ? sum * (1.0f / 3.0f) : 0.25f * sum));
+}
+
+// 1 / x from the hardware's approximate reciprocal refined by one
+// Newton-Raphson step for 1/x (r <- r (2 - x r), written r + r (1 - x r)):
+// the relative error squares, from about 2^-22 to below the FP32 rounding
+// of the result; no slow path for special values (x is a density or a
+// relaxation time, positive and of order one).
+__device__ __forceinline__ float recip(float x) {
+  const float r = __fdividef(1.0f, x);
+  return fmaf(r, fmaf(-x, r, 1.0f), r);
 }
 
 // Per-lattice constants of the collision, in registers.
@@ -220,8 +226,10 @@ __device__ __forceinline__ void collide_cell(const float (&fr)[9], const float (
   // where neighbours are close (no cancellation of O(10) terms)
   const float lap = (2.0f / 3.0f) * ((pE - pC) + (pN - pC) + (pW - pC) + (pS - pC)) +
                     (1.0f / 6.0f) * ((pNE - pC) + (pNW - pC) + (pSW - pC) + (pSE - pC));
-  const float gx = (pE - pW) * (1.0f / 3.0f) + (pNE - pNW - pSW + pSE) * (1.0f / 12.0f);
-  const float gy = (pN - pS) * (1.0f / 3.0f) + (pNE + pNW - pSW - pSE) * (1.0f / 12.0f);
+  // gradient: (nE - sW) and (nW - sE) shared by both components
+  const float dA_ = pNE - pSW, dB_ = pNW - pSE;
+  const float gx = (pE - pW) * (1.0f / 3.0f) + (dA_ - dB_) * (1.0f / 12.0f);
+  const float gy = (pN - pS) * (1.0f / 3.0f) + (dA_ + dB_) * (1.0f / 12.0f);
   const float mu = K.A4 * phi * ((phi - K.phis) * (phi + K.phis)) - K.kappa * lap;
   float C = 0.5f * (phi * K.inv_phis + 1.0f);
   C = fminf(fmaxf(C, 0.0f), 1.0f);
@@ -230,31 +238,40 @@ __device__ __forceinline__ void collide_cell(const float (&fr)[9], const float (
   // fr holds deviations f_i - w_i n0: their sum is n - n0
   const float dn = fr[0] + fr[1] + fr[2] + fr[3] + fr[4] + fr[5] + fr[6] + fr[7] + fr[8];
   n = K.n0 + dn;
+  // n - (n0 + dn) exactly (n0 > |dn|: the error of the rounded sum is
+  // representable), carried into 1 / n to first order
+  const float n_lo = dn - (n - K.n0);
   const float mx = fr[1] - fr[3] + fr[5] - fr[6] - fr[7] + fr[8];
   const float my = fr[2] - fr[4] + fr[5] + fr[6] - fr[7] - fr[8];
-  const float inv_n = __frcp_rn(n);  // 1 / n, correctly rounded
+  const float inv_hi = recip(n);
+  const float inv_n = fmaf(-n_lo * inv_hi, inv_hi, inv_hi);
   const float ux = (mx + 0.5f * Fx) * inv_n;
   uy = (my + 0.5f * Fy) * inv_n;
   u2 = ux * ux + uy * uy;
-  const float om = __frcp_rn(0.5f + 3.0f * (K.nu_air + C * K.dnu));
-  const float pref = 3.0f * (1.0f - 0.5f * om);
+  const float om = recip(0.5f + 3.0f * (K.nu_air + C * K.dnu));
+  const float pref = 3.0f - 1.5f * om;  // 3 (1 - 1 / (2 tau)): the forcing prefactor over c_s^2
   // A_i - n0 = 3 (phi mu + n / 3) - n0 for i >= 1 (Eq. 6), on deviations
   const float p3 = dn + 3.0f * phi * mu;
   const float uF = ux * Fx + uy * Fy;
-  const float base = -1.5f * u2;  // velocity-independent part of the bracket of Eq. 5
   // Moving directions first (deviations feq_i - w_i n0); the rest direction
   // then takes the balance, feq_0 - w_0 n0 = (n - n0) - sum_{i>=1} (feq_i -
   // w_i n0) and F_0 = -sum_{i>=1} F_i.  This equals A_0 of Eq. 6 (the
   // moments of Eq. 5-6 and of the forcing term are exact) but conserves
   // mass in FP32, whose rounded weights 4/9, 1/9, 1/36 do not sum to one.
   // Opposite directions i, i' share the even part of the equilibrium and of
-  // the forcing term and differ in the sign of the odd part: feq = E +- O,
-  // F = FE +- FO with E = w (p3 + n (base + 4.5 cu^2)), O = 3 w n cu,
-  // FE = w pref (3 cu cF - uF), FO = w pref cF.  The collision
-  // f* = (1 - om) f + om feq + F then reads f*_i = (1 - om) f_i + A +- B
-  // with A = om E + FE and B = om O + FO.
-  float sumA = 0.0f;
-  const float omc = 1.0f - om, on3 = om * 3.0f * n;
+  // the forcing term and differ in the sign of the odd part: with cu = c_i.u
+  // and cF = c_i.F, the collision f* = (1 - om) f + om feq + F reads
+  //   f*_i = (1 - om) f_i + w (a +- b),
+  //   a = om (p3 + n (4.5 cu^2 - 1.5 u^2)) + pref (3 cu cF - u.F)
+  //     = a0 + cu (a1 cu + a2 cF),
+  //   b = 3 om n cu + pref cF = b1 cu + pref cF,
+  // with a0 = om (p3 - 1.5 n u^2) - pref u.F, a1 = 4.5 om n, a2 = 3 pref,
+  // b1 = 3 om n (Eq. 5 for feq, Eq. 4's forcing term).
+  const float omn = om * n;
+  const float a0 = fmaf(om, fmaf(-1.5f * n, u2, p3), -pref * uF);
+  const float a1 = 4.5f * omn, a2 = 3.0f * pref, b1 = 3.0f * omn;
+  const float omc = 1.0f - om;
+  float sum1 = 0.0f, sum2 = 0.0f;  // a of the axis / diagonal pairs
 #pragma unroll
   for (int i = 1; i < 9; i++) {
     if (i == 3 || i == 4 || i == 7 || i == 8) continue;  // handled with its pair
@@ -263,16 +280,13 @@ __device__ __forceinline__ void collide_cell(const float (&fr)[9], const float (
     const float ex = (float)cEX(i), ey = (float)cEY(i);
     const float cu = ex * ux + ey * uy;
     const float cF = ex * Fx + ey * Fy;
-    const float E = w * fmaf(n, fmaf(4.5f * cu, cu, base), p3);
-    const float wp = w * pref;
-    const float FE = wp * fmaf(3.0f * cu, cF, -uF);
-    const float A = fmaf(om, E, FE);
-    const float B = fmaf(w * on3, cu, wp * cF);
-    sumA += A;
-    fs[i] = fmaf(omc, fr[i], A + B);
-    fs[ib] = fmaf(omc, fr[ib], A - B);
+    const float a = fmaf(cu, fmaf(a1, cu, a2 * cF), a0);
+    const float b = fmaf(b1, cu, pref * cF);
+    if (i < 5) sum1 += a; else sum2 += a;
+    fs[i] = fmaf(omc, fr[i], w * (a + b));
+    fs[ib] = fmaf(omc, fr[ib], w * (a - b));
   }
-  fs[0] = fmaf(omc, fr[0], fmaf(om, dn, -2.0f * sumA));
+  fs[0] = fmaf(omc, fr[0], fmaf(om, dn, -2.0f * fmaf(W1, sum1, W2 * sum2)));
   // order parameter: Eq. 9-10 with the rest direction special; the moving
   // part q g_i + Omega_i streams, (1 - q) g_i stays
   const float gmu = K.gamma * mu;
@@ -368,8 +382,20 @@ __global__ void __launch_bounds__(32, kStepBlocksPerSM)
     const int ckA = column_kind(I, xA), ckB = column_kind(I, xB);
     const int ckW = column_kind(I, wrapi(uA - 1, nx));  // west of A
     const int ckE = column_kind(I, wrapi(uB + 1, nx));  // east of B
-    // lanes whose cells or neighbours may be solid (bounce-back, ghosts)
-    const bool colmay = geom == GEOM_PLATE || (geom == GEOM_NOZZLE && (ckW | ckA | ckB | ckE) != 0);
+    // Kinds of the lane's four columns W (west of A), A, B, E (east of B) in
+    // one row, 2 bits each (W lowest); the last four rows R .. R-3 are kept
+    // in one word, row R in the low byte.  A row's kinds follow from its
+    // mapped row m alone: nozzle rows below L take the columns' kinds, plate
+    // rows below wt are solid (the top one wetting), rows outside a closed
+    // domain are non-wetting solids.
+    const unsigned ckpack = (unsigned)ckW | ((unsigned)ckA << 2) | ((unsigned)ckB << 4) |
+                            ((unsigned)ckE << 6);
+    auto row_bits = [&](int m) -> unsigned {
+      if (m < 0) return 0x55u;
+      if (geom == GEOM_NOZZLE) return m < L ? ckpack : 0u;
+      if (geom == GEOM_PLATE) return m < wt ? (m == wt - 1 ? 0xAAu : 0x55u) : 0u;
+      return 0u;
+    };
     // lane 0's A / lane 31's B on a wall column: the column outside (xo)
     const bool edge = (lane == 0 && ckA != 0) || (lane == 31 && ckB != 0);
     const int xo = lane == 0 ? wrapi(uA - 1, nx) : wrapi(uB + 1, nx);
@@ -498,14 +524,14 @@ __global__ void __launch_bounds__(32, kStepBlocksPerSM)
     auto load_outer = [&](int slot) -> float {
       const float* o = so + slot * RG::OW + (lane == 0 ? 0 : 10);
       const int wd = (ODD || lane == 31) ? 0 : 1;  // lane 0: the odd column of its pair
-      if (!H) return o[wd] + o[2 + wd] + o[4 + wd] + o[6 + wd] + o[8 + wd];
-      float s = o[wd];
+      if (!H) return o[wd] + ((o[2 + wd] + o[4 + wd]) + (o[6 + wd] + o[8 + wd]));
+      float s = 0.0f;  // g_1..4 first, as for the lane's own columns
 #pragma unroll
       for (int i = 1; i < 5; i++) {
         const __half2 hp = *reinterpret_cast<const __half2*>(o + 2 * i);
         s += wd ? __high2float(hp) : __low2float(hp);
       }
-      return s;
+      return o[wd] + s;
     };
 
 #pragma unroll
@@ -513,12 +539,16 @@ __global__ void __launch_bounds__(32, kStepBlocksPerSM)
 
     // raw phi of rows R, R-1, R-2 (pr*0..2) and of the outer column (px*);
     // phi with ghosts of rows R-1, R-2, R-3 (pe*0..2) and of the columns
-    // west of A (peW*) and east of B (peE*); mapped rows R .. R-3 (m0..m3)
+    // west of A (peW*) and east of B (peE*); mapped rows R .. R-2 (m0..m2),
+    // packed kinds of rows R .. R-3 (kp)
     float prA0 = 0.f, prA1 = 0.f, prA2 = 0.f, prB0 = 0.f, prB1 = 0.f, prB2 = 0.f;
     float px0 = 0.f, px1 = 0.f, px2 = 0.f;
     float peA0 = 0.f, peA1 = 0.f, peA2 = 0.f, peB0 = 0.f, peB1 = 0.f, peB2 = 0.f;
     float peW0 = 0.f, peW1 = 0.f, peW2 = 0.f, peE0 = 0.f, peE1 = 0.f, peE2 = 0.f;
-    int m0 = -1, m1 = -1, m2 = -1, m3 = -1;
+    int m0 = -1, m1 = -1, m2 = -1;
+    unsigned kp = 0x55555555u;
+    // kind of column c (0 W, 1 A, 2 B, 3 E) in row R - j
+#define KD(c, j) ((int)((kp >> (8 * (j) + 2 * (c))) & 3u))
     // gathered pulls of the row being streamed, per column: f_0..3, f_5,
     // f_6 and g_0..4 (g_4 without its moving part yet); the upward movers
     // for the next row (f_2 own, f_5 from the west, f_6 from the east, the
@@ -539,25 +569,26 @@ __global__ void __launch_bounds__(32, kStepBlocksPerSM)
       const int R = y0 - 3 + k;
       stage(R + P, gw, R + P - 2, fw);
       cp_async_wait<P>();  // this lane's copies of g row R and f row R-2 have landed
-      m3 = m2;
       m2 = m1;
       m1 = m0;
       {
         int ym;
         m0 = map_row_v(R, ny, bc, ym) ? ym : -1;
       }
+      kp = (kp << 8) | row_bits(m0);
       prA2 = prA1; prA1 = prA0; prB2 = prB1; prB1 = prB0;
       px2 = px1; px1 = px0;
       peA2 = peA1; peA1 = peA0; peB2 = peB1; peB1 = peB0;
       peW2 = peW1; peW1 = peW0; peE2 = peE1; peE1 = peE0;
-      const int kA0 = kind_m(geom, ckA, L, wt, m0), kB0 = kind_m(geom, ckB, L, wt, m0);
-      const int kA1 = kind_m(geom, ckA, L, wt, m1), kB1 = kind_m(geom, ckB, L, wt, m1);
+      const int kA0 = KD(1, 0), kB0 = KD(2, 0), kA1 = KD(1, 1), kB1 = KD(2, 1);
       // ---- raw phi of row R
       {
         float ga[5], gb[5];
         load_g(gr, ga, gb);
-        prA0 = kA0 == 0 ? ga[0] + ga[1] + ga[2] + ga[3] + ga[4] : 0.0f;
-        prB0 = kB0 == 0 ? gb[0] + gb[1] + gb[2] + gb[3] + gb[4] : 0.0f;
+        // phi = g_0 + the small g_1..4, added first: one rounding at the
+        // scale of phi* instead of four
+        prA0 = kA0 == 0 ? ga[0] + ((ga[1] + ga[2]) + (ga[3] + ga[4])) : 0.0f;
+        prB0 = kB0 == 0 ? gb[0] + ((gb[1] + gb[2]) + (gb[3] + gb[4])) : 0.0f;
         px0 = 0.0f;
         if (any_edge && edge && m0 >= 0 && row_kind(geom, cke, L, wt, m0) != 0 &&
             row_kind(geom, cko, L, wt, m0) == 0)
@@ -566,7 +597,7 @@ __global__ void __launch_bounds__(32, kStepBlocksPerSM)
       // ---- phi with wetting ghosts of row R-1
       peA0 = prA1;
       peB0 = prB1;
-      if (__any_sync(kFull, (kA1 | kB1) != 0)) {
+      if (__any_sync(kFull, ((kp >> 8) & 0x3Cu) != 0u)) {
         float wN = __shfl_up_sync(kFull, prB0, 1), wC = __shfl_up_sync(kFull, prB1, 1);
         float wS = __shfl_up_sync(kFull, prB2, 1);
         float eN = __shfl_down_sync(kFull, prA0, 1), eC = __shfl_down_sync(kFull, prA1, 1);
@@ -576,10 +607,9 @@ __global__ void __launch_bounds__(32, kStepBlocksPerSM)
         } else if (edge) {
           eN = px0; eC = px1; eS = px2;
         }
-        const int kA2 = kind_m(geom, ckA, L, wt, m2), kB2 = kind_m(geom, ckB, L, wt, m2);
-        const int kW0 = kind_m(geom, ckW, L, wt, m0), kW1 = kind_m(geom, ckW, L, wt, m1);
-        const int kW2 = kind_m(geom, ckW, L, wt, m2), kE0 = kind_m(geom, ckE, L, wt, m0);
-        const int kE1 = kind_m(geom, ckE, L, wt, m1), kE2 = kind_m(geom, ckE, L, wt, m2);
+        const int kA2 = KD(1, 2), kB2 = KD(2, 2);
+        const int kW0 = KD(0, 0), kW1 = KD(0, 1), kW2 = KD(0, 2);
+        const int kE0 = KD(3, 0), kE1 = KD(3, 1), kE2 = KD(3, 2);
         if (kA1 != 0)
           peA0 = ghost_phi(kA1, hk, prB1, kB1, prA0, kA0, wC, kW1, prA2, kA2, prB0, kB0, wN, kW0,
                            wS, kW2, prB2, kB2);
@@ -598,7 +628,7 @@ __global__ void __launch_bounds__(32, kStepBlocksPerSM)
       }
       // ---- collision of row Rc = R-2 (both columns)
       const int Rc = R - 2;
-      const int kA2 = kind_m(geom, ckA, L, wt, m2), kB2 = kind_m(geom, ckB, L, wt, m2);
+      const int kA2 = KD(1, 2), kB2 = KD(2, 2);
       float fsA[9], fsB[9], gPA[4], gPB[4], gSA[4], gSB[4], g0A, g0B;
       float dg[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       {
@@ -653,18 +683,15 @@ __global__ void __launch_bounds__(32, kStepBlocksPerSM)
       const float sh3 = __shfl_down_sync(kFull, fsA[3], 1), shP3 = __shfl_down_sync(kFull, gPA[2], 1);
       const float sh5 = __shfl_up_sync(kFull, fsB[5], 1), sh6 = __shfl_down_sync(kFull, fsA[6], 1);
       // does any lane have a solid source among rows Rc-1 .. Rc (warp-uniform)
-      const bool solid_rows = __any_sync(
-          kFull, m2 < 0 || m3 < 0 ||
-                     (colmay && ((geom == GEOM_NOZZLE && (m2 < L || m3 < L)) ||
-                                 (geom == GEOM_PLATE && (m2 < wt || m3 < wt)))));
+      const bool solid_rows = __any_sync(kFull, (kp >> 16) != 0u);
       // ---- row Y = R-3: downward movers of row Rc, bounce-back, store
       if (k >= 6) {
         const int Y = R - 3;
         float f4A = fsA[4], f7A = fsB[7], f8A = sh8, p4A = gPA[3];
         float f4B = fsB[4], f7B = sh7, f8B = fsA[8], p4B = gPB[3];
-        const int kA3 = kind_m(geom, ckA, L, wt, m3), kB3 = kind_m(geom, ckB, L, wt, m3);
+        const int kA3 = KD(1, 3), kB3 = KD(2, 3);  // row Y
         if (solid_rows) {
-          const int kW2 = kind_m(geom, ckW, L, wt, m2), kE2 = kind_m(geom, ckE, L, wt, m2);
+          const int kW2 = KD(0, 2), kE2 = KD(3, 2);
           // sources (x, Y+1), (x+1, Y+1), (x-1, Y+1)
           if (kA2 != 0) { f4A = upA[0]; p4A = upA[3]; }
           if (kB2 != 0) { f7A = bbA[0]; }
@@ -673,13 +700,28 @@ __global__ void __launch_bounds__(32, kStepBlocksPerSM)
           if (kE2 != 0) { f7B = bbB[0]; }
           if (kA2 != 0) { f8B = bbB[1]; }
         }
-        const bool sA = wA && kA3 == 0, sB = wB && kB3 == 0;
-        const float fA[9] = {aA[0], aA[1], aA[2], aA[3], f4A, aA[4], aA[5], f7A, f8A};
-        const float fB[9] = {aB[0], aB[1], aB[2], aB[3], f4B, aB[4], aB[5], f7B, f8B};
-        const float gA[5] = {aA[6], aA[7], aA[8], aA[9], aA[10] + p4A};
-        const float gB[5] = {aB[6], aB[7], aB[8], aB[9], aB[10] + p4B};
+        // Solid cells of the written columns are written too, with the 0
+        // they hold (their populations are never read as such): every store
+        // then covers whole column pairs and no DRAM sector is left partly
+        // written (which costs a read-modify-write).
+        float fA[9] = {aA[0], aA[1], aA[2], aA[3], f4A, aA[4], aA[5], f7A, f8A};
+        float fB[9] = {aB[0], aB[1], aB[2], aB[3], f4B, aB[4], aB[5], f7B, f8B};
+        float gA[5] = {aA[6], aA[7], aA[8], aA[9], aA[10] + p4A};
+        float gB[5] = {aB[6], aB[7], aB[8], aB[9], aB[10] + p4B};
+        if (solid_rows) {
+#pragma unroll
+          for (int i = 0; i < 9; i++) {
+            fA[i] = kA3 == 0 ? fA[i] : 0.0f;
+            fB[i] = kB3 == 0 ? fB[i] : 0.0f;
+          }
+#pragma unroll
+          for (int i = 0; i < 5; i++) {
+            gA[i] = kA3 == 0 ? gA[i] : 0.0f;
+            gB[i] = kB3 == 0 ? gB[i] : 0.0f;
+          }
+        }
         const int cA = Y * nx + xA, cB = Y * nx + xB;
-        if (!ODD && sA && sB) {
+        if (!ODD && wA && wB) {
           if (!H) {
 #pragma unroll
             for (int i = 0; i < 9; i++)
@@ -700,27 +742,27 @@ __global__ void __launch_bounds__(32, kStepBlocksPerSM)
           }
         } else {
           if (!H) {
-            if (sA) {
+            if (wA) {
 #pragma unroll
               for (int i = 0; i < 9; i++) fout[(size_t)i * N + cA] = fA[i];
 #pragma unroll
               for (int i = 0; i < 5; i++) gout[(size_t)i * N + cA] = gA[i];
             }
-            if (sB) {
+            if (wB) {
 #pragma unroll
               for (int i = 0; i < 9; i++) fout[(size_t)i * N + cB] = fB[i];
 #pragma unroll
               for (int i = 0; i < 5; i++) gout[(size_t)i * N + cB] = gB[i];
             }
           } else {
-            if (sA) {
+            if (wA) {
 #pragma unroll
               for (int i = 0; i < 9; i++) fhout[(size_t)i * N + cA] = __float2half_rn(fA[i]);
               gout[cA] = gA[0];
 #pragma unroll
               for (int i = 1; i < 5; i++) ghout[(size_t)(i - 1) * N + cA] = __float2half_rn(gA[i]);
             }
-            if (sB) {
+            if (wB) {
 #pragma unroll
               for (int i = 0; i < 9; i++) fhout[(size_t)i * N + cB] = __float2half_rn(fB[i]);
               gout[cB] = gB[0];
@@ -740,9 +782,8 @@ __global__ void __launch_bounds__(32, kStepBlocksPerSM)
         float f1B = fsA[1], f3B = sh3, f2B = upB[0], f5B = upB[1], f6B = upB[2];
         float p1B = gPA[0], p3B = shP3, p2B = upB[3];
         if (solid_rows) {
-          const int kW2 = kind_m(geom, ckW, L, wt, m2), kE2 = kind_m(geom, ckE, L, wt, m2);
-          const int kA3 = kind_m(geom, ckA, L, wt, m3), kB3 = kind_m(geom, ckB, L, wt, m3);
-          const int kW3 = kind_m(geom, ckW, L, wt, m3), kE3 = kind_m(geom, ckE, L, wt, m3);
+          const int kW2 = KD(0, 2), kE2 = KD(3, 2);
+          const int kA3 = KD(1, 3), kB3 = KD(2, 3), kW3 = KD(0, 3), kE3 = KD(3, 3);
           // A: sources (x-1, Rc) = W, (x+1, Rc) = B, (x, Rc-1) = A,
           // (x-1, Rc-1) = W, (x+1, Rc-1) = B
           if (kW2 != 0) { f1A = fsA[3]; p1A = gPA[2]; }
@@ -774,6 +815,7 @@ __global__ void __launch_bounds__(32, kStepBlocksPerSM)
       fr_ = fr_ + 1 == RG::DF ? 0 : fr_ + 1;
       fw = fw + 1 == RG::DF ? 0 : fw + 1;
     }
+#undef KD
     cp_async_wait<0>();  // no copy may land after the warp moves on
     if (DIAG && lane == 0) {
       atomicAdd(I.sums + 0, acc_n);
@@ -1211,7 +1253,32 @@ cudaError_t launch_step(const Inst* d_inst, const Item* d_items, int n_items, in
 #undef LAUNCH_STEP
 }
 
-int step_prefetch_for(int) { return 2; }
+int step_prefetch_for(int) { return 1; }
+
+int step_slots(int prefetch, bool h16, bool odd) {
+  int dev = 0, sms = 0, nb = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 1;
+  const size_t smem = step_smem_bytes(kStepThreads, prefetch, h16);
+  cudaError_t e;
+#define SLOTS_P(PF)                                                                          \
+  e = h16 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step_kernel<false, PF, true, false>, \
+                                                          kStepThreads, smem)               \
+          : odd ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(                            \
+                      &nb, step_kernel<false, PF, false, true>, kStepThreads, smem)          \
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(                            \
+                      &nb, step_kernel<false, PF, false, false>, kStepThreads, smem);
+  switch (prefetch) {
+    case 1: SLOTS_P(1) break;
+    case 2: SLOTS_P(2) break;
+    case 3: SLOTS_P(3) break;
+    default: SLOTS_P(4) break;
+  }
+#undef SLOTS_P
+  if (e != cudaSuccess || nb < 1) return sms > 0 ? sms : 1;
+  return sms * nb;
+}
 
 cudaError_t set_step_smem_limit() {
   const int lim = (int)step_smem_bytes(kStepThreads, kMaxPrefetch, false);
