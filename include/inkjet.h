@@ -220,12 +220,14 @@ ij_status ij_kernel_timing(ij_handle h, int enable, double* total_ms, long long*
  *                equal cost near one S-th of the total (one wave that ends
  *                together), the rest into short pieces listed last; -1: the
  *                whole strip in equal pieces, no tail; -2: 3/4 and a tail of
- *                shorter pieces.
+ *                shorter pieces; -3, -4, -5: the whole strip in pieces for 2,
+ *                3, 4 full waves.
  *
- * ij_tune      -- set chunk (>= -2) and prefetch (block_size: 32, or <= 0
+ * ij_tune      -- set chunk (>= -5) and prefetch (block_size: 32, or <= 0
  *                 for every bucket).  Synchronises.
  * ij_autotune  -- time `reps` trial launches of every candidate (chunks
- *                 8..256 and 0, -1, -2; prefetch 1..4) on the current state
+ *                 8..128 in steps of 8, 160, 192, 256 and 0 .. -5; prefetch
+ *                 1..4) on the current state
  *                 and keep the fastest.  Trial launches leave the state and
  *                 the time unchanged.  Synchronises.
  * ij_get_tuning -- block size, chunk, prefetch and item count of bucket
@@ -274,7 +276,7 @@ ij_status ij_get_tuning(ij_handle h, int bucket, int* block_size, int* chunk, in
  *                   IJ_ERR_PARAM.  The call is asynchronous.
  * Limits: ny <= 8192 and at most 16384 work items (strips of 60 columns times
  * chunks of 64 rows); larger lattices are rejected with IJ_ERR_PARAM.
- * Descriptors and scratch live in one fixed device array of about 0.6 MB per
+ * Descriptors and scratch live in one fixed device array of about 0.7 MB per
  * GPU that loads the library, kept until the process exits.  The first call
  * on a device looks up that array's device address, so make it before any
  * stream capture.  Every call shares the array: calls whose GPU work

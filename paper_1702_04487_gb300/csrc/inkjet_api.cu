@@ -346,22 +346,25 @@ int strip_wall_rows(const Inst& I, const Item& it) {
 // becomes a tail of short pieces listed after all bodies, which the SMs
 // that finish first take up.  Variants: chunk 0 (beta 7/8, tail pieces of a
 // sixth of a body piece), -1 (beta 1, no tail), -2 (beta 3/4, tail pieces of
-// an eighth).
+// an eighth), -3 .. -5 (beta 1, pieces for 2 .. 4 full waves).
 constexpr double kWallCost = 1.2;
 
 void balanced_items(ij_handle h, const Bucket& b, int slots) {
   const int variant = -b.chunk;
-  const double beta = variant == 1 ? 1.0 : (variant == 2 ? 0.75 : 0.875);
+  // variants 3..5: the whole strip in equal pieces making 2..4 full waves
+  const int waves = variant >= 3 ? variant - 1 : 1;
+  slots *= waves;
+  const double beta = variant == 0 ? 0.875 : (variant == 2 ? 0.75 : 1.0);
   const double tail_div = variant == 2 ? 8.0 : 6.0;
   struct Strip { Item it; int wall; double cost; };
   std::vector<Strip> strips;
   double C = 0.0;
   for (int k = 0; k < h->n_inst; k++) {
     const Inst& I = h->inst[k];
-    const int n = items_per_range(I, I.ny, 0, I.ny);
+    const int n = items_per_range(I, I.ny, 0, I.ny, false);
     const size_t at = h->items.size();
     h->items.resize(at + n);
-    make_items_range(I, k, I.ny, 0, I.ny, h->items.data() + at, n);
+    make_items_range(I, k, I.ny, 0, I.ny, h->items.data() + at, n, false);
     for (int j = 0; j < n; j++) {
       Strip st;
       st.it = h->items[at + j];
@@ -395,6 +398,10 @@ void balanced_items(ij_handle h, const Bucket& b, int slots) {
     return std::max(0, std::min(st.it.ch, (int)lround(y)));
   };
   std::vector<Item> tail;
+  // body pieces, listed round-robin over the strips (piece j of every strip,
+  // then piece j + 1), so that each wave spans every strip
+  std::vector<std::vector<Item>> pieces(strips.size());
+  int max_pieces = 0;
   for (size_t i = 0; i < strips.size(); i++) {
     const Strip& st = strips[i];
     const double body = beta * st.cost;
@@ -405,9 +412,10 @@ void balanced_items(ij_handle h, const Bucket& b, int slots) {
       Item it = st.it;
       it.y0 = y;
       it.ch = ye - y;
-      h->items.push_back(it);
+      pieces[i].push_back(it);
       y = ye;
     }
+    max_pieces = std::max(max_pieces, (int)pieces[i].size());
     const int tn = std::max(4, (int)lround(T / tail_div));  // rows per tail piece
     for (; y < st.it.ch; y += tn) {
       Item it = st.it;
@@ -416,6 +424,9 @@ void balanced_items(ij_handle h, const Bucket& b, int slots) {
       tail.push_back(it);
     }
   }
+  for (int j = 0; j < max_pieces; j++)
+    for (size_t i = 0; i < strips.size(); i++)
+      if (j < (int)pieces[i].size()) h->items.push_back(pieces[i][j]);
   h->items.insert(h->items.end(), tail.begin(), tail.end());
 }
 
@@ -444,10 +455,10 @@ void build_items(ij_handle h) {
         const int split = I.ny - I.ny / 8;
         const int ya = pass == 0 ? 0 : split, yb = pass == 0 ? split : I.ny;
         const int ch = pass == 0 ? b.chunk : tail_chunk;
-        const int n = items_per_range(I, ch, ya, yb);
+        const int n = items_per_range(I, ch, ya, yb, true);
         const size_t at = h->items.size();
         h->items.resize(at + n);
-        make_items_range(I, k, ch, ya, yb, h->items.data() + at, n);
+        make_items_range(I, k, ch, ya, yb, h->items.data() + at, n, true);
       }
     }
     // Items of nozzle-wall strips below the nozzle exit cost more per row
@@ -455,7 +466,7 @@ void build_items(ij_handle h) {
     // as long, so that no SM is left with a long one of them at the end.
     auto costly = [&](const Item& it) {
       const Inst& I = h->inst[it.inst];
-      if (I.geom != GEOM_NOZZLE || it.y0 > I.L + 1) return false;
+      if (it.half || I.geom != GEOM_NOZZLE || it.y0 > I.L + 1) return false;
       const int x0 = it.xs - it.halo, x1 = it.xs + it.nout + it.halo;  // columns held
       // either wall band [cx0 - wt, cx0) or [cx1, cx1 + wt) among them
       return (x1 > I.cx0 - I.wt && x0 < I.cx0) || (x1 > I.cx1 && x0 < I.cx1 + I.wt);
@@ -1094,8 +1105,8 @@ ij_status ij_tune(ij_handle h, int block_size, int chunk, int prefetch) {
   ij_status st = check_handle(h);
   if (st != IJ_OK) return st;
   if (h->is3d) return fail(IJ_ERR_PARAM, "3-D handles have no launch shape to tune");
-  if (chunk < -2 || prefetch < 1 || prefetch > kMaxPrefetch)
-    return fail(IJ_ERR_PARAM, "chunk must be >= -2 and prefetch in 1..%d", kMaxPrefetch);
+  if (chunk < -5 || prefetch < 1 || prefetch > kMaxPrefetch)
+    return fail(IJ_ERR_PARAM, "chunk must be >= -5 and prefetch in 1..%d", kMaxPrefetch);
   bool found = false;
   for (Bucket& b : h->buckets)
     if (block_size <= 0 || b.nthreads == block_size) {
@@ -1119,7 +1130,8 @@ ij_status ij_autotune(ij_handle h, int reps) {
   if (h->poisoned) return fail(IJ_ERR_STATE, "handle is poisoned");
   if (h->is3d) return IJ_OK;  // the 3-D kernels have one fixed launch shape
   // row chunks, then the cost-balanced variants (chunk <= 0)
-  static const int kChunks[] = {8, 16, 24, 32, 48, 64, 96, 128, 256, 0, -1, -2};
+  static const int kChunks[] = {8,   16,  24,  32,  40,  48, 56, 64, 72, 80, 88, 96, 104,
+                                112, 120, 128, 160, 192, 256, 0,  -1, -2, -3, -4, -5};
   cudaEvent_t e0, e1;
   CUDA_TRY(cudaEventCreate(&e0));
   CUDA_TRY(cudaEventCreate(&e1));

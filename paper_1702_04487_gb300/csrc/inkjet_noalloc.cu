@@ -12,7 +12,7 @@
 //
 // The array below is sized for one lattice of at most kMaxRows rows and
 // kMaxItems work items; every GPU that loads the library holds it (about
-// 0.6 MB) until the process exits.  All calls on a device share it and it
+// 0.7 MB) until the process exits.  All calls on a device share it and it
 // keeps the last call's contents, so each call clears the parts that must
 // start at zero, and calls whose GPU work overlaps (for example on two
 // streams) race on it.

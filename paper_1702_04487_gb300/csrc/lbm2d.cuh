@@ -48,9 +48,12 @@ struct Inst {
 // A unit of work of the step kernel (one warp): `ch` rows starting at y0 of
 // the strip of lattice `inst` that writes columns xs .. xs + nout - 1
 // (nout <= 60); lane l holds columns xs - halo + 2 l and the next one
-// (periodic wrap, halo = 2).
+// (periodic wrap, halo = 2).  Half-warp items (half = 1, nout <= 28): lanes
+// 0-15 take rows y0 .. y0+ch-1 and lanes 16-31 rows y1 .. y1+ch-1 of the
+// same strip (y1 < 0: lanes 16-31 idle), lane l holding columns
+// xs - halo + 2 (l mod 16) and the next one.
 struct Item {
-  int inst, xs, nout, halo, y0, ch;
+  int inst, xs, nout, halo, y0, ch, half, y1;
 };
 
 constexpr int kStepThreads = 32;  // one warp per block, one work item each
@@ -62,13 +65,16 @@ size_t step_smem_bytes(int nthreads, int prefetch, bool h16);
 size_t state_bytes_f(const Inst& I);
 size_t state_bytes_g(const Inst& I);
 cudaError_t set_step_smem_limit();
-// Work items of one lattice (row chunks of `chunk` rows x strips) into out
-// (at most cap); returns the count, or -1 when cap is too small.
+// Work items of one lattice (row chunks of `chunk` rows x strips, a narrow
+// last strip in half-warp items) into out (at most cap); returns the count,
+// or -1 when cap is too small.
 int make_items(const Inst& I, int k, int chunk, Item* out, int cap);
 int items_per_lattice(const Inst& I, int chunk);
-// The same for rows ya .. yb-1 only.
-int make_items_range(const Inst& I, int k, int chunk, int ya, int yb, Item* out, int cap);
-int items_per_range(const Inst& I, int chunk, int ya, int yb);
+// The same for rows ya .. yb-1 only (allow_half: narrow strips in half-warp
+// items; out may be null to count).
+int make_items_range(const Inst& I, int k, int chunk, int ya, int yb, Item* out, int cap,
+                     bool allow_half);
+int items_per_range(const Inst& I, int chunk, int ya, int yb, bool allow_half);
 
 // host helpers of inkjet_api.cu
 ij_status validate_params(const ij_params& p, int k);

@@ -24,6 +24,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <algorithm>
+
 #include "lbm2d.cuh"
 
 namespace ij {
@@ -135,6 +137,34 @@ __device__ __forceinline__ void cp4(unsigned sa, const void* p, size_t strideB) 
       " cp.async.ca.shared.global [%0+%8], [%4], %5;\n}\n" ::"r"(sa),
       "l"(q), "l"(q + strideB), "l"(q + 2 * strideB), "l"(q + 3 * strideB), "n"(B), "n"(SS),
       "n"(2 * SS), "n"(3 * SS)
+      : "memory");
+}
+// The same, issued only when pred is set (one predicate for the group).
+template <int B, int SS>
+__device__ __forceinline__ void cp5_if(unsigned sa, const void* p, size_t strideB, bool pred) {
+  const char* q = static_cast<const char*>(p);
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %6, 0;\n"
+      " @p cp.async.ca.shared.global [%0], [%1], %7;\n"
+      " @p cp.async.ca.shared.global [%0+%8], [%2], %7;\n"
+      " @p cp.async.ca.shared.global [%0+%9], [%3], %7;\n"
+      " @p cp.async.ca.shared.global [%0+%10], [%4], %7;\n"
+      " @p cp.async.ca.shared.global [%0+%11], [%5], %7;\n}\n" ::"r"(sa),
+      "l"(q), "l"(q + strideB), "l"(q + 2 * strideB), "l"(q + 3 * strideB), "l"(q + 4 * strideB),
+      "r"((int)pred), "n"(B), "n"(SS), "n"(2 * SS), "n"(3 * SS), "n"(4 * SS)
+      : "memory");
+}
+template <int B, int SS>
+__device__ __forceinline__ void cp4_if(unsigned sa, const void* p, size_t strideB, bool pred) {
+  const char* q = static_cast<const char*>(p);
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %5, 0;\n"
+      " @p cp.async.ca.shared.global [%0], [%1], %6;\n"
+      " @p cp.async.ca.shared.global [%0+%7], [%2], %6;\n"
+      " @p cp.async.ca.shared.global [%0+%8], [%3], %6;\n"
+      " @p cp.async.ca.shared.global [%0+%9], [%4], %6;\n}\n" ::"r"(sa),
+      "l"(q), "l"(q + strideB), "l"(q + 2 * strideB), "l"(q + 3 * strideB), "r"((int)pred),
+      "n"(B), "n"(SS), "n"(2 * SS), "n"(3 * SS)
       : "memory");
 }
 // One predicated copy of B bytes.
@@ -316,7 +346,10 @@ __device__ __forceinline__ void collide_cell(const float (&fr)[9], const float (
 // (their populations stream into the strip), and xs - 2, xs + nout + 1 only
 // give phi to the stencil.  A solid edge column (lane 0's A, lane 31's B)
 // needs phi beyond the strip for its ghost value: that lane also stages the
-// g of the column outside.  Neighbours along x: the other column of the lane,
+// g of the column outside.  Half-warp items (a strip of nout <= 28 columns):
+// lanes 0-15 and 16-31 each hold the strip, on the row ranges y0 and y1 of
+// the same length, with every shuffle confined to its 16 lanes -- a narrow
+// last strip of a lattice then takes half a warp per row.  Neighbours along x: the other column of the lane,
 // or the neighbouring lane's by warp shuffle; along y: registers, as the warp
 // marches up the rows.
 //
@@ -348,8 +381,9 @@ struct StepRing {
   // FP32 then g_1..4 [4][32] half pairs, f [9][32] half pairs
   static constexpr int GW = H ? 192 : 320;
   static constexpr int FW = H ? 288 : 576;
-  // outer column of the edge lanes: [lane 0, lane 31][5 values, 2 words each]
-  static constexpr int OW = 20;
+  // outer column of the edge lanes: [4 edge lanes (0, 31, or 0, 15, 16, 31
+  // in half-warp items)][5 values, 2 words each]
+  static constexpr int OW = 40;
 };
 
 template <bool DIAG, int P, bool H, bool ODD>
@@ -376,8 +410,12 @@ __global__ void __launch_bounds__(32, kStepBlocksPerSM)
     if (__shfl_sync(kFull, st0, 0) & kStatusNumeric) continue;
     const int nx = I.nx, ny = I.ny, geom = I.geom, L = I.L, wt = I.wt, bc = I.bc;
     const int N = nx * ny;  // < 2^31 / 9 (checked on the host)
-    const int y0 = it.y0, ch = it.ch;
-    const int uA = it.xs - 2 + 2 * lane, uB = uA + 1;  // unwrapped columns
+    // half-warp items: width 16, half h on rows from y1; an empty second half
+    // (y1 < 0) stages, collides and writes nothing
+    const int wid = it.half ? 16 : 32, ll = lane & (wid - 1), hh = it.half ? lane >> 4 : 0;
+    const bool act = hh == 0 || it.y1 >= 0;
+    const int y0 = hh ? it.y1 : it.y0, ch = it.ch;
+    const int uA = it.xs - 2 + 2 * ll, uB = uA + 1;  // unwrapped columns
     const int xA = wrapi(uA, nx), xB = wrapi(uB, nx);
     const int ckA = column_kind(I, xA), ckB = column_kind(I, xB);
     const int ckW = column_kind(I, wrapi(uA - 1, nx));  // west of A
@@ -396,16 +434,20 @@ __global__ void __launch_bounds__(32, kStepBlocksPerSM)
       if (geom == GEOM_PLATE) return m < wt ? (m == wt - 1 ? 0xAAu : 0x55u) : 0u;
       return 0u;
     };
-    // lane 0's A / lane 31's B on a wall column: the column outside (xo)
-    const bool edge = (lane == 0 && ckA != 0) || (lane == 31 && ckB != 0);
-    const int xo = lane == 0 ? wrapi(uA - 1, nx) : wrapi(uB + 1, nx);
-    const int cko = lane == 0 ? ckW : ckE, cke = lane == 0 ? ckA : ckB;
+    // the first lane's A / the last lane's B (of the warp or half-warp) on a
+    // wall column: the column outside (xo); eo: the lane's outer slot
+    const bool lft = ll == 0, rgt = ll == wid - 1;
+    const bool edge = (lft && ckA != 0) || (rgt && ckB != 0);
+    const int xo = lft ? wrapi(uA - 1, nx) : wrapi(uB + 1, nx);
+    const int cko = lft ? ckW : ckE, cke = lft ? ckA : ckB;
+    const int eo = 2 * hh + (lft ? 0 : 1);
     const bool any_edge = __any_sync(kFull, edge);
     const bool dA = geom != GEOM_NOZZLE || (xA >= I.cx0 && xA < I.cx1);
     const bool dB = geom != GEOM_NOZZLE || (xB >= I.cx0 && xB < I.cx1);
     const int xe = it.xs + it.nout;
-    const bool vA = uA >= it.xs - 1 && uA <= xe, vB = uB >= it.xs - 1 && uB <= xe;  // results used
-    const bool wA = uA >= it.xs && uA < xe, wB = uB >= it.xs && uB < xe;            // written
+    const bool vA = act && uA >= it.xs - 1 && uA <= xe;  // collision results used
+    const bool vB = act && uB >= it.xs - 1 && uB <= xe;
+    const bool wA = act && uA >= it.xs && uA < xe, wB = act && uB >= it.xs && uB < xe;  // written
     CollK K;
     K.phis = I.phis;
     K.inv_phis = I.inv_phis;
@@ -432,27 +474,31 @@ __global__ void __launch_bounds__(32, kStepBlocksPerSM)
     __half* __restrict__ ghout = reinterpret_cast<__half*>(gout + N);
 
     // Stage g of row rg into g slot sgs and f of row rf into f slot sfs (one
-    // cp.async group; rows outside the item's needs or a closed domain are
-    // skipped, warp-uniformly).
-    auto stage = [&](int rg, int sgs, int rf, int sfs) {
-      int ym;
-      if (rg <= y0 + ch + 2 && map_row_v(rg, ny, bc, ym)) {
+    // cp.async group).  Whether a row is needed depends on the iteration only
+    // (both halves of a half-warp item have ch rows); a row outside a closed
+    // domain is skipped lane by lane (the halves of a half-warp item sit on
+    // different rows).  kg: stage g (iteration k + P <= ch + 5); kf: stage f
+    // (4 <= k + P <= ch + 5).
+    auto stage = [&](bool kg, int rg, int sgs, bool kf, int rf, int sfs) {
+      int ym = 0;
+      if (kg) {
+        const bool ok = act && map_row_v(rg, ny, bc, ym);
         const unsigned d = sg_a + sgs * (RG::GW * 4);
         const int c = ym * nx + xA;
         if (ODD) {
-          cp5<4, 256>(d + lane * 8, gin + c, (size_t)N * 4);
-          cp5<4, 256>(d + lane * 8 + 4, gin + ym * nx + xB, (size_t)N * 4);
+          cp5_if<4, 256>(d + lane * 8, gin + c, (size_t)N * 4, ok);
+          cp5_if<4, 256>(d + lane * 8 + 4, gin + ym * nx + xB, (size_t)N * 4, ok);
         } else if (!H) {
-          cp5<8, 256>(d + lane * 8, gin + c, (size_t)N * 4);
+          cp5_if<8, 256>(d + lane * 8, gin + c, (size_t)N * 4, ok);
         } else {
-          cp1_if<8>(d + lane * 8, gin + c, true);
-          cp4<4, 128>(d + 256 + lane * 4, ghin + c, (size_t)N * 2);
+          cp1_if<8>(d + lane * 8, gin + c, ok);
+          cp4_if<4, 128>(d + 256 + lane * 4, ghin + c, (size_t)N * 2, ok);
         }
         if (any_edge) {
           // a solid edge column next to a fluid one outside the strip
-          const bool need = edge && row_kind(geom, cke, L, wt, ym) != 0 &&
+          const bool need = ok && edge && row_kind(geom, cke, L, wt, ym) != 0 &&
                             row_kind(geom, cko, L, wt, ym) == 0;
-          const unsigned o = so_a + sgs * (RG::OW * 4) + (lane == 0 ? 0 : 40);
+          const unsigned o = so_a + sgs * (RG::OW * 4) + eo * 40;
           const int co = ym * nx + (ODD ? xo : (xo & ~1));
           if (!H) {
 #pragma unroll
@@ -466,21 +512,22 @@ __global__ void __launch_bounds__(32, kStepBlocksPerSM)
           }
         }
       }
-      if (rf >= y0 - 1 && rf <= y0 + ch && map_row_v(rf, ny, bc, ym)) {
+      if (kf) {
+        const bool ok = act && map_row_v(rf, ny, bc, ym);
         const unsigned d = sf_a + sfs * (RG::FW * 4);
         const int c = ym * nx + xA;
         if (ODD) {
-          cp5<4, 256>(d + lane * 8, fin + c, (size_t)N * 4);
-          cp4<4, 256>(d + 5 * 256 + lane * 8, fin + 5 * (size_t)N + c, (size_t)N * 4);
+          cp5_if<4, 256>(d + lane * 8, fin + c, (size_t)N * 4, ok);
+          cp4_if<4, 256>(d + 5 * 256 + lane * 8, fin + 5 * (size_t)N + c, (size_t)N * 4, ok);
           const int cb = ym * nx + xB;
-          cp5<4, 256>(d + lane * 8 + 4, fin + cb, (size_t)N * 4);
-          cp4<4, 256>(d + 5 * 256 + lane * 8 + 4, fin + 5 * (size_t)N + cb, (size_t)N * 4);
+          cp5_if<4, 256>(d + lane * 8 + 4, fin + cb, (size_t)N * 4, ok);
+          cp4_if<4, 256>(d + 5 * 256 + lane * 8 + 4, fin + 5 * (size_t)N + cb, (size_t)N * 4, ok);
         } else if (!H) {
-          cp5<8, 256>(d + lane * 8, fin + c, (size_t)N * 4);
-          cp4<8, 256>(d + 5 * 256 + lane * 8, fin + 5 * (size_t)N + c, (size_t)N * 4);
+          cp5_if<8, 256>(d + lane * 8, fin + c, (size_t)N * 4, ok);
+          cp4_if<8, 256>(d + 5 * 256 + lane * 8, fin + 5 * (size_t)N + c, (size_t)N * 4, ok);
         } else {
-          cp5<4, 128>(d + lane * 4, fhin + c, (size_t)N * 2);
-          cp4<4, 128>(d + 5 * 128 + lane * 4, fhin + 5 * (size_t)N + c, (size_t)N * 2);
+          cp5_if<4, 128>(d + lane * 4, fhin + c, (size_t)N * 2, ok);
+          cp4_if<4, 128>(d + 5 * 128 + lane * 4, fhin + 5 * (size_t)N + c, (size_t)N * 2, ok);
         }
       }
       cp_async_commit();
@@ -522,8 +569,8 @@ __global__ void __launch_bounds__(32, kStepBlocksPerSM)
     };
     // raw phi of the outer column (edge lanes)
     auto load_outer = [&](int slot) -> float {
-      const float* o = so + slot * RG::OW + (lane == 0 ? 0 : 10);
-      const int wd = (ODD || lane == 31) ? 0 : 1;  // lane 0: the odd column of its pair
+      const float* o = so + slot * RG::OW + eo * 10;
+      const int wd = (ODD || !lft) ? 0 : 1;  // the first lane: the odd column of its pair
       if (!H) return o[wd] + ((o[2 + wd] + o[4 + wd]) + (o[6 + wd] + o[8 + wd]));
       float s = 0.0f;  // g_1..4 first, as for the lane's own columns
 #pragma unroll
@@ -535,7 +582,8 @@ __global__ void __launch_bounds__(32, kStepBlocksPerSM)
     };
 
 #pragma unroll
-    for (int j = 0; j < P; j++) stage(y0 - 3 + j, j, y0 - 5 + j, j);
+    for (int j = 0; j < P; j++)
+      stage(j <= ch + 5, y0 - 3 + j, j, j >= 4 && j <= ch + 5, y0 - 5 + j, j);
 
     // raw phi of rows R, R-1, R-2 (pr*0..2) and of the outer column (px*);
     // phi with ghosts of rows R-1, R-2, R-3 (pe*0..2) and of the columns
@@ -560,14 +608,15 @@ __global__ void __launch_bounds__(32, kStepBlocksPerSM)
     for (int i = 0; i < 4; i++) upA[i] = upB[i] = 0.f;
     bbA[0] = bbA[1] = bbB[0] = bbB[1] = 0.f;
     double acc_n = 0.0, acc_phi = 0.0, acc_mom = 0.0;
-    int gr = 0, gw = P, fr_ = 0, fw = P;  // ring slots: g of row R / R+P, f of row R-2 / R+P-2
-    if (gw >= RG::DG) gw -= RG::DG;
-    if (fw >= RG::DF) fw -= RG::DF;
 
 #pragma unroll 1
     for (int k = 0; k < ch + 6; k++) {
       const int R = y0 - 3 + k;
-      stage(R + P, gw, R + P - 2, fw);
+      // ring slots (compile-time moduli): g of row R / R+P, f of row R-2 / R+P-2
+      const unsigned ku = (unsigned)k;
+      const int gr = ku % RG::DG, gw = (ku + P) % RG::DG;
+      const int fr_ = ku % RG::DF, fw = (ku + P) % RG::DF;
+      stage(k + P <= ch + 5, R + P, gw, k + P >= 4 && k + P <= ch + 5, R + P - 2, fw);
       cp_async_wait<P>();  // this lane's copies of g row R and f row R-2 have landed
       m2 = m1;
       m1 = m0;
@@ -598,11 +647,11 @@ __global__ void __launch_bounds__(32, kStepBlocksPerSM)
       peA0 = prA1;
       peB0 = prB1;
       if (__any_sync(kFull, ((kp >> 8) & 0x3Cu) != 0u)) {
-        float wN = __shfl_up_sync(kFull, prB0, 1), wC = __shfl_up_sync(kFull, prB1, 1);
-        float wS = __shfl_up_sync(kFull, prB2, 1);
-        float eN = __shfl_down_sync(kFull, prA0, 1), eC = __shfl_down_sync(kFull, prA1, 1);
-        float eS = __shfl_down_sync(kFull, prA2, 1);
-        if (edge && lane == 0) {
+        float wN = __shfl_up_sync(kFull, prB0, 1, wid), wC = __shfl_up_sync(kFull, prB1, 1, wid);
+        float wS = __shfl_up_sync(kFull, prB2, 1, wid);
+        float eN = __shfl_down_sync(kFull, prA0, 1, wid), eC = __shfl_down_sync(kFull, prA1, 1, wid);
+        float eS = __shfl_down_sync(kFull, prA2, 1, wid);
+        if (edge && lft) {
           wN = px0; wC = px1; wS = px2;
         } else if (edge) {
           eN = px0; eC = px1; eS = px2;
@@ -617,15 +666,9 @@ __global__ void __launch_bounds__(32, kStepBlocksPerSM)
           peB0 = ghost_phi(kB1, hk, eC, kE1, prB0, kB0, prA1, kA1, prB2, kB2, eN, kE0, prA0, kA0,
                            prA2, kA2, eS, kE2);
       }
-      peW0 = __shfl_up_sync(kFull, peB0, 1);
-      peE0 = __shfl_down_sync(kFull, peA0, 1);
-      if (k < 4) {
-        gr = gr + 1 == RG::DG ? 0 : gr + 1;
-        gw = gw + 1 == RG::DG ? 0 : gw + 1;
-        fr_ = fr_ + 1 == RG::DF ? 0 : fr_ + 1;
-        fw = fw + 1 == RG::DF ? 0 : fw + 1;
-        continue;  // warp-uniform: rows below y0 - 1 do not collide
-      }
+      peW0 = __shfl_up_sync(kFull, peB0, 1, wid);
+      peE0 = __shfl_down_sync(kFull, peA0, 1, wid);
+      if (k < 4) continue;  // warp-uniform: rows below y0 - 1 do not collide
       // ---- collision of row Rc = R-2 (both columns)
       const int Rc = R - 2;
       const int kA2 = KD(1, 2), kB2 = KD(2, 2);
@@ -633,9 +676,7 @@ __global__ void __launch_bounds__(32, kStepBlocksPerSM)
       float dg[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       {
         float ga[5], gb[5], fa[9], fb[9];
-        int s2 = gr - 2;
-        if (s2 < 0) s2 += RG::DG;
-        load_g(s2, ga, gb);
+        load_g((ku + RG::DG - 2) % RG::DG, ga, gb);
         load_f(fr_, fa, fb);
         const bool drv = geom != GEOM_NOZZLE || (m2 >= 0 && m2 < L);
         float nA, uyA, u2A, nB, uyB, u2B;
@@ -646,7 +687,7 @@ __global__ void __launch_bounds__(32, kStepBlocksPerSM)
         // only fluid cells whose results are used raise the flag or count
         const bool cA = vA && kA2 == 0, cB = vB && kB2 == 0;
         if ((cA && !(u2A < 0.09f)) || (cB && !(u2B < 0.09f))) atomicOr(I.status, kStatusNumeric);
-        if (DIAG && Rc >= y0 && Rc < y0 + ch) {
+        if (DIAG && k >= 5 && k < ch + 5) {  // Rc in [y0, y0 + ch)
           const bool oA = cA && wA, oB = cB && wB;
           const float eA = fminf(fmaxf(prA2 * K.inv_phis, 0.0f), 1.0f);
           const float eB = fminf(fmaxf(prB2 * K.inv_phis, 0.0f), 1.0f);
@@ -660,14 +701,13 @@ __global__ void __launch_bounds__(32, kStepBlocksPerSM)
           }
         }
       }
-      if (DIAG && Rc >= y0 && Rc < y0 + ch) {
+      if (DIAG && k >= 5 && k < ch + 5) {
         // the strip's cells of the row are summed in FP32, every total
         // across strips, rows and chunks in FP64
+        for (int o = wid >> 1; o > 0; o >>= 1)
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-          for (int j = 0; j < 6; j++) dg[j] += __shfl_down_sync(kFull, dg[j], o);
-        if (lane == 0) {
+          for (int j = 0; j < 6; j++) dg[j] += __shfl_down_sync(kFull, dg[j], o, wid);
+        if (ll == 0 && act) {
           atomicAdd(I.rows + Rc, (double)dg[0]);
           atomicAdd(I.rows + ny + Rc, (double)dg[1]);
           atomicAdd(I.rows + 2 * ny + Rc, (double)dg[2]);
@@ -677,11 +717,14 @@ __global__ void __launch_bounds__(32, kStepBlocksPerSM)
         }
       }
       // movers that cross to the neighbouring lane
-      const float sh7 = __shfl_down_sync(kFull, fsA[7], 1);  // f*_7 of B's east neighbour
-      const float sh8 = __shfl_up_sync(kFull, fsB[8], 1);    // f*_8 of A's west neighbour
-      const float sh1 = __shfl_up_sync(kFull, fsB[1], 1), shP1 = __shfl_up_sync(kFull, gPB[0], 1);
-      const float sh3 = __shfl_down_sync(kFull, fsA[3], 1), shP3 = __shfl_down_sync(kFull, gPA[2], 1);
-      const float sh5 = __shfl_up_sync(kFull, fsB[5], 1), sh6 = __shfl_down_sync(kFull, fsA[6], 1);
+      const float sh7 = __shfl_down_sync(kFull, fsA[7], 1, wid);  // f*_7 of B's east neighbour
+      const float sh8 = __shfl_up_sync(kFull, fsB[8], 1, wid);    // f*_8 of A's west neighbour
+      const float sh1 = __shfl_up_sync(kFull, fsB[1], 1, wid);
+      const float shP1 = __shfl_up_sync(kFull, gPB[0], 1, wid);
+      const float sh3 = __shfl_down_sync(kFull, fsA[3], 1, wid);
+      const float shP3 = __shfl_down_sync(kFull, gPA[2], 1, wid);
+      const float sh5 = __shfl_up_sync(kFull, fsB[5], 1, wid);
+      const float sh6 = __shfl_down_sync(kFull, fsA[6], 1, wid);
       // does any lane have a solid source among rows Rc-1 .. Rc (warp-uniform)
       const bool solid_rows = __any_sync(kFull, (kp >> 16) != 0u);
       // ---- row Y = R-3: downward movers of row Rc, bounce-back, store
@@ -810,14 +853,10 @@ __global__ void __launch_bounds__(32, kStepBlocksPerSM)
         bbA[0] = fsA[5]; bbA[1] = fsA[6];
         bbB[0] = fsB[5]; bbB[1] = fsB[6];
       }
-      gr = gr + 1 == RG::DG ? 0 : gr + 1;
-      gw = gw + 1 == RG::DG ? 0 : gw + 1;
-      fr_ = fr_ + 1 == RG::DF ? 0 : fr_ + 1;
-      fw = fw + 1 == RG::DF ? 0 : fw + 1;
     }
 #undef KD
     cp_async_wait<0>();  // no copy may land after the warp moves on
-    if (DIAG && lane == 0) {
+    if (DIAG && ll == 0 && act) {
       atomicAdd(I.sums + 0, acc_n);
       atomicAdd(I.sums + 1, acc_phi);
       atomicAdd(I.sums + 2, acc_mom);
@@ -1159,7 +1198,7 @@ __global__ void f_convert_kernel(const Inst* __restrict__ insts, int index, cons
 // ---------------------------------------------------------------------------
 size_t step_smem_bytes(int nthreads, int prefetch, bool h16) {
   // per warp: g ring (P+3 rows) with the edge lanes' outer column, f ring (P+1 rows)
-  const int gw = h16 ? 192 : 320, fw = h16 ? 288 : 576, ow = 20;
+  const int gw = h16 ? 192 : 320, fw = h16 ? 288 : 576, ow = 40;
   return (size_t)(nthreads / 32) * ((prefetch + 3) * (gw + ow) + (prefetch + 1) * fw) * sizeof(float);
 }
 
@@ -1297,32 +1336,58 @@ cudaError_t set_step_smem_limit() {
   return e;
 }
 
-int make_items_range(const Inst& I, int k, int chunk, int ya, int yb, Item* out, int cap) {
-  constexpr int halo = 2, W = kStripCols;  // 60 written columns per strip (2 per lane)
+// Items of one strip over rows ya .. yb-1 in chunks of `chunk` rows.  A
+// narrow strip (nout <= 28, allow_half) pairs consecutive full-length chunks
+// into half-warp items; a chunk left over (odd count or the short last one)
+// is a half-warp item of its own.  Writes up to cap items into out (out may
+// be null to count); returns the count.
+int strip_items(const Inst& I, int k, int xs, int nout, int chunk, int ya, int yb, bool allow_half,
+                Item* out, int cap) {
+  constexpr int halo = 2;
+  int n = 0;
+  auto put = [&](int y0, int ch, int half, int y1) {
+    if (out && n < cap) out[n] = Item{k, xs, nout, halo, y0, ch, half, y1};
+    n++;
+  };
+  if (!allow_half || nout > kStripCols / 2 - 2) {
+    for (int y0 = ya; y0 < yb; y0 += chunk) put(y0, yb - y0 < chunk ? yb - y0 : chunk, 0, -1);
+    return n;
+  }
+  int y0 = ya;
+  for (; y0 + 2 * chunk <= yb; y0 += 2 * chunk) put(y0, chunk, 1, y0 + chunk);
+  for (; y0 < yb; y0 += chunk) put(y0, yb - y0 < chunk ? yb - y0 : chunk, 1, -1);
+  return n;
+}
+
+int make_items_range(const Inst& I, int k, int chunk, int ya, int yb, Item* out, int cap,
+                     bool allow_half) {
+  const int W = kStripCols;  // 60 written columns per full strip (2 per lane)
   const int nstrip = (I.nx + W - 1) / W;
   int n = 0;
+  // row-major: the strips of one chunk of rows next to each other (items
+  // that run together share halo sectors and DRAM pages)
   for (int y0 = ya; y0 < yb; y0 += chunk)
     for (int s = 0; s < nstrip; s++) {
-      if (n >= cap) return -1;
-      Item& it = out[n++];
-      it.inst = k;
-      it.xs = s * W;
-      it.nout = I.nx - s * W < W ? I.nx - s * W : W;
-      it.halo = halo;
-      it.y0 = y0;
-      it.ch = yb - y0 < chunk ? yb - y0 : chunk;
+      const int xs = s * W, nout = I.nx - xs < W ? I.nx - xs : W;
+      const bool half = allow_half && nout <= W / 2 - 2;
+      if (half && ((y0 - ya) / chunk) % 2 == 1) continue;  // taken with the chunk below
+      const int y1 = half ? std::min(yb, y0 + 2 * chunk) : std::min(yb, y0 + chunk);
+      const int m = strip_items(I, k, xs, nout, chunk, y0, y1, allow_half, out ? out + n : nullptr,
+                                out ? cap - n : 0);
+      if (out && n + m > cap) return -1;
+      n += m;
     }
   return n;
 }
 
 int make_items(const Inst& I, int k, int chunk, Item* out, int cap) {
-  return make_items_range(I, k, chunk, 0, I.ny, out, cap);
+  return make_items_range(I, k, chunk, 0, I.ny, out, cap, true);
 }
 
-int items_per_range(const Inst& I, int chunk, int ya, int yb) {
-  return yb > ya ? ((I.nx + kStripCols - 1) / kStripCols) * ((yb - ya + chunk - 1) / chunk) : 0;
+int items_per_range(const Inst& I, int chunk, int ya, int yb, bool allow_half) {
+  return yb > ya ? make_items_range(I, 0, chunk, ya, yb, nullptr, 0, allow_half) : 0;
 }
 
-int items_per_lattice(const Inst& I, int chunk) { return items_per_range(I, chunk, 0, I.ny); }
+int items_per_lattice(const Inst& I, int chunk) { return items_per_range(I, chunk, 0, I.ny, true); }
 
 }  // namespace ij
