@@ -213,25 +213,42 @@ def oracle_sample(params):
     return OracleSim(p), p, "one %dx%d lattice (lattice 0 of the workload)" % (p["nx"], p["ny"])
 
 
-def cpu_baseline(params, seconds=12.0):
-    """The FP64 oracle, as it stands, on one lattice of the workload."""
-    sim, p, what = oracle_sample(params)
-    cells = cells_of(dict(p, dim=params[0].get("dim", 2)))
+def _time_oracle(sim, seconds):
+    """Steps the oracle for about `seconds`; returns (steps, wall seconds)."""
     t0 = time.perf_counter()
     sim.step(1)
     per = time.perf_counter() - t0
     n = max(1, int(seconds / max(per, 1e-6)))
     t0 = time.perf_counter()
     sim.step(n)
-    dt = time.perf_counter() - t0
-    return {"value": cells * n / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": "%d steps of %s, FP64, single-threaded C" % (n, what)}
+    return n, time.perf_counter() - t0
+
+
+def cpu_baseline(params, seconds=12.0):
+    """The FP64 oracle, as it stands, on one lattice of the workload: on all
+    host cores (its independent per-cell passes under OpenMP) and on one."""
+    from oracle import set_threads, threads
+    all_cores = threads()
+    sim, p, what = oracle_sample(params)
+    cells = cells_of(dict(p, dim=params[0].get("dim", 2)))
+    n, dt = _time_oracle(sim, seconds / 2)
+    set_threads(1)
+    try:
+        sim1, _, _ = oracle_sample(params)
+        n1, dt1 = _time_oracle(sim1, seconds / 2)
+    finally:
+        set_threads(all_cores)
+    return {"value": cells * n / dt / 1e6, "unit": "MLUPS", "cores": all_cores, "kind": "oracle",
+            "sample": "%d steps of %s, FP64 C oracle, per-cell passes on %d OpenMP threads"
+                      % (n, what, all_cores),
+            "single_thread": {"value": cells * n1 / dt1 / 1e6, "cores": 1, "steps": n1}}
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    from oracle import threads
     params, desc = workload(args.workload)
     sim, p, what = oracle_sample(params)
     cells = cells_of(dict(p, dim=params[0].get("dim", 2)))
@@ -240,14 +257,16 @@ def run_reference(args):
     sim.step(args.steps)
     dt = time.perf_counter() - t0
     value = cells * args.steps / dt / 1e6
-    sample = "each step: one time step of %s, FP64 oracle, single-threaded C" % what
+    cores = threads()
+    sample = ("each step: one time step of %s, FP64 C oracle, per-cell passes on %d OpenMP "
+              "threads" % (what, cores))
     print(json.dumps({
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "impl": "reference",
         "config": {"workload": desc, "lattices": len(params), "cells_per_step": cells},
-        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
@@ -289,14 +308,20 @@ def run_native(args):
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
+    # the K-step region, timed `repeats` times (each a barrier and a
+    # synchronise on both sides); the median over repeats is reported
     n0 = inkjet.ij_launch_count(h)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    inkjet.ij_step(h, args.steps)
-    ev1.record(stream)
-    barrier()
-    ms = ev0.elapsed_time(ev1)
-    launches = inkjet.ij_launch_count(h) - n0
+    rep_ms = []
+    for _ in range(args.repeats):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        ev0.record(stream)
+        inkjet.ij_step(h, args.steps)
+        ev1.record(stream)
+        barrier()
+        rep_ms.append(max_over_ranks(ev0.elapsed_time(ev1), world, "cuda"))
+    launches = (inkjet.ij_launch_count(h) - n0) // args.repeats
+    ms = statistics.median(rep_ms)
     # the step kernel's own launch durations: CUDA events recorded on the
     # handle's stream around every step-kernel launch of a second timed run
     # (launch by launch, so outside the graph replay)
@@ -307,7 +332,7 @@ def run_native(args):
     clk = clocks.stop()
     obs, _ = inkjet.ij_observe(h, 0, phi=False)
     inkjet.ij_destroy(h)
-    ms_max = max_over_ranks(ms, world, "cuda")
+    ms_max = ms  # median over repeats of the slowest rank's time
     value = job_mlups(cells, args.steps, world, ms_max / 1e3)
 
     # ---- end to end through the public API, host buffers
@@ -342,6 +367,8 @@ def run_native(args):
         line = {
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "repeats": {"count": args.repeats, "ms_per_step": [m / args.steps for m in rep_ms],
+                        "reported": "median"},
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if kind in ("2d", "3d32") else "f32 (f16 storage)",
             "data": "synthetic",
@@ -516,6 +543,8 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--repeats", type=int, default=5,
+                    help="times the K-step region is timed; the median is reported")
     ap.add_argument("--impl", choices=("native", "reference"), default="native")
     ap.add_argument("--workload", choices=("cfg2", "cfg2h", "big", "cfg3", "cfg4", "cfg4h", "e1"),
                     default="cfg2")

@@ -95,8 +95,10 @@ struct ij_handle_s {
   ij_free_fn free_fn = nullptr;
   void* ctx = nullptr;
   std::vector<void*> blocks;
-  // CUDA graph of one diagnostics period (diag_every steps, or 16)
-  cudaStream_t cap_stream = nullptr;
+  // CUDA graph of one diagnostics period (diag_every steps, or 16); the
+  // diagnostics record runs on a branch (cap_stream2) beside the next steps
+  cudaStream_t cap_stream = nullptr, cap_stream2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaGraphExec_t gexec = nullptr;
   int graph_steps = 0;
   long long graph_launches = 0;  // kernels per graph launch
@@ -143,7 +145,11 @@ struct ij_handle_s {
     drain_events();
     drop_graph();
     if (cap_stream) cudaStreamDestroy(cap_stream);
-    cap_stream = nullptr;
+    if (cap_stream2) cudaStreamDestroy(cap_stream2);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+    cap_stream = cap_stream2 = nullptr;
+    ev_fork = ev_join = nullptr;
     for (void* p : blocks) {
       if (free_fn) free_fn(p, ctx); else cudaFree(p);
     }
@@ -596,11 +602,19 @@ ij_status one_step(ij_handle h) {
 // Capture one diagnostics period into a graph: the step kernels of every
 // bucket with time offsets 0..P-1 (offset 0 with diagnostics when enabled),
 // the record kernel after the first step, and one advance of the time by P.
+// In 2-D the record kernel runs on a branch of its own beside steps 1..P-1:
+// it reads only the FP64 row and lattice sums of step 0 (and resets them)
+// and the time, which those steps do not touch; the branch joins before the
+// advance of the time.
 ij_status build_graph(ij_handle h) {
   h->drop_graph();
   const int P = h->diag_every > 0 ? h->diag_every : 16;
   if (!h->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  if (!h->cap_stream2) CUDA_TRY(cudaStreamCreateWithFlags(&h->cap_stream2, cudaStreamNonBlocking));
+  if (!h->ev_fork) CUDA_TRY(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+  if (!h->ev_join) CUDA_TRY(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
   cudaStream_t cs = h->cap_stream;
+  bool branched = false;
   CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
   long long n = 0;
   cudaError_t e = cudaSuccess;
@@ -617,10 +631,15 @@ ij_status build_graph(ij_handle h) {
       if (e != cudaSuccess) break;
     }
     if (diag && e == cudaSuccess) {
-      e = launch_finalize(h->d_inst, h->n_inst, h->d_t, cs);
+      e = cudaEventRecord(h->ev_fork, cs);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(h->cap_stream2, h->ev_fork, 0);
+      if (e == cudaSuccess) e = launch_finalize(h->d_inst, h->n_inst, h->d_t, h->cap_stream2);
+      if (e == cudaSuccess) e = cudaEventRecord(h->ev_join, h->cap_stream2);
+      branched = e == cudaSuccess;
       n++;
     }
   }
+  if (branched && e == cudaSuccess) e = cudaStreamWaitEvent(cs, h->ev_join, 0);
   if (e == cudaSuccess) {
     e = launch_advance(h->d_t, P, cs);
     n++;

@@ -18,8 +18,9 @@
 //  - geometry is analytic (no mask array);
 //  - storage is FP32, or FP16 (f as offsets from w_i n0, g_1..4 as is, g_0
 //    in FP32) with every update in FP32;
-//  - diagnostics rows (ink weight, mass, momentum) are summed in FP32 per
-//    strip row and in FP64 across rows and strips, on diagnostics steps.
+//  - diagnostics rows (ink weight e, e n, e n u_y) are summed in FP32 per
+//    strip row and in FP64 across strips; the lattice totals of n, phi and
+//    n u_y in FP32 per lane over an item and in FP64 across lanes and items.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -607,7 +608,11 @@ __global__ void __launch_bounds__(32, kStepBlocksPerSM)
 #pragma unroll
     for (int i = 0; i < 4; i++) upA[i] = upB[i] = 0.f;
     bbA[0] = bbA[1] = bbB[0] = bbB[1] = 0.f;
-    double acc_n = 0.0, acc_phi = 0.0, acc_mom = 0.0;
+    // lattice totals sum n, sum phi, sum n u_y of the lane's cells over the
+    // item (diagnostics steps), in FP64: a sum of a few hundred FP32 values
+    // is exact in FP64, so the totals do not depend on how rows are cut into
+    // items (only on the FP64 order of the final additions)
+    double sn = 0.0, sphi = 0.0, smom = 0.0;
 
 #pragma unroll 1
     for (int k = 0; k < ch + 6; k++) {
@@ -673,7 +678,7 @@ __global__ void __launch_bounds__(32, kStepBlocksPerSM)
       const int Rc = R - 2;
       const int kA2 = KD(1, 2), kB2 = KD(2, 2);
       float fsA[9], fsB[9], gPA[4], gPB[4], gSA[4], gSB[4], g0A, g0B;
-      float dg[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      float dg[3] = {0.f, 0.f, 0.f};  // row sums of e, e n, e n u_y
       {
         float ga[5], gb[5], fa[9], fb[9];
         load_g((ku + RG::DG - 2) % RG::DG, ga, gb);
@@ -693,11 +698,11 @@ __global__ void __launch_bounds__(32, kStepBlocksPerSM)
           const float eB = fminf(fmaxf(prB2 * K.inv_phis, 0.0f), 1.0f);
           if (oA) {
             dg[0] += eA; dg[1] += eA * nA; dg[2] += eA * nA * uyA;
-            dg[3] += nA; dg[4] += prA2; dg[5] += nA * uyA;
+            sn += (double)nA; sphi += (double)prA2; smom += (double)(nA * uyA);
           }
           if (oB) {
             dg[0] += eB; dg[1] += eB * nB; dg[2] += eB * nB * uyB;
-            dg[3] += nB; dg[4] += prB2; dg[5] += nB * uyB;
+            sn += (double)nB; sphi += (double)prB2; smom += (double)(nB * uyB);
           }
         }
       }
@@ -706,14 +711,11 @@ __global__ void __launch_bounds__(32, kStepBlocksPerSM)
         // across strips, rows and chunks in FP64
         for (int o = wid >> 1; o > 0; o >>= 1)
 #pragma unroll
-          for (int j = 0; j < 6; j++) dg[j] += __shfl_down_sync(kFull, dg[j], o, wid);
+          for (int j = 0; j < 3; j++) dg[j] += __shfl_down_sync(kFull, dg[j], o, wid);
         if (ll == 0 && act) {
           atomicAdd(I.rows + Rc, (double)dg[0]);
           atomicAdd(I.rows + ny + Rc, (double)dg[1]);
           atomicAdd(I.rows + 2 * ny + Rc, (double)dg[2]);
-          acc_n += (double)dg[3];
-          acc_phi += (double)dg[4];
-          acc_mom += (double)dg[5];
         }
       }
       // movers that cross to the neighbouring lane
@@ -856,10 +858,18 @@ __global__ void __launch_bounds__(32, kStepBlocksPerSM)
     }
 #undef KD
     cp_async_wait<0>();  // no copy may land after the warp moves on
-    if (DIAG && ll == 0 && act) {
-      atomicAdd(I.sums + 0, acc_n);
-      atomicAdd(I.sums + 1, acc_phi);
-      atomicAdd(I.sums + 2, acc_mom);
+    if (DIAG) {
+      double tn = sn, tphi = sphi, tmom = smom;
+      for (int o = wid >> 1; o > 0; o >>= 1) {
+        tn += __shfl_down_sync(kFull, tn, o, wid);
+        tphi += __shfl_down_sync(kFull, tphi, o, wid);
+        tmom += __shfl_down_sync(kFull, tmom, o, wid);
+      }
+      if (ll == 0 && act) {
+        atomicAdd(I.sums + 0, tn);
+        atomicAdd(I.sums + 1, tphi);
+        atomicAdd(I.sums + 2, tmom);
+      }
     }
   }
 }
