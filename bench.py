@@ -33,10 +33,8 @@ FALLBACK_HBM_GBS = 6800.0
 # workload, by row chunk, valid only for the sources (kernel_hash) recorded
 # with them.
 NCU_TRAFFIC = {
-    "cfg2": {"kernel_sha": "a59b0987d8b42d16",
-             "bytes_per_step": {48: 749.13e6, 64: 748.50e6, 96: 747.14e6, 128: 735.26e6}},
-    "cfg2h": {"kernel_sha": "a59b0987d8b42d16",
-              "bytes_per_step": {48: 393.10e6, 64: 392.01e6, 96: 390.86e6, 128: 388.70e6}},
+    "cfg2": {"kernel_sha": "4a250ca1ad18cfdb", "bytes_per_step": {80: 721.65e6}},
+    "cfg2h": {"kernel_sha": "4a250ca1ad18cfdb", "bytes_per_step": {80: 368.85e6}},
 }
 
 
