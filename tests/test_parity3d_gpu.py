@@ -198,6 +198,12 @@ def test_small_nozzle3_breakup_fp32(ij, oracle_run3):
     pre = ho[:, 0] < tb_o - 50
     assert np.abs(hg[pre, 3] - ho[pre, 3]).max() < 1e-3 * np.abs(ho[:, 3]).max()
     assert np.abs(hg[pre, 4] - ho[pre, 4]).max() < 1e-2 * ho[0, 4]
+    # the leading droplet's velocity (record column 8) within 1 % of the
+    # oracle's just after pinch-off and at the end of the run, and its volume
+    after = int(np.searchsorted(ho[:, 0], tb_o)) + 1
+    for r in (after, len(ho) - 1):
+        assert abs(hg[r, 8] - ho[r, 8]) <= 0.01 * abs(ho[r, 8]), (r, hg[r, 8], ho[r, 8])
+        assert abs(hg[r, 6] - ho[r, 6]) <= 0.01 * ho[r, 6], (r, hg[r, 6], ho[r, 6])
 
 
 def test_small_nozzle3_fp16_error_report(ij, oracle_run3):
