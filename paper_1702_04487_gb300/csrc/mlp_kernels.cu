@@ -7,14 +7,17 @@
 // GEMM shape: C[M x N] = A[M x K] B[N x K]^T with A and B row-major (K
 // contiguous, "K-major").  A CTA of 128 threads owns a 128 x BN tile of C,
 // BN in {16, 32, 64, 128, 256}.  K advances in slices of 64 (128 bytes of
-// BF16, one row of a 128-byte swizzle atom), double-buffered in shared
-// memory.  One thread drives the pipeline: it loads a slice of A and of B
-// with the tensor memory accelerator (cp.async.bulk.tensor, 128-byte
-// swizzle written by the copy itself, completion counted in bytes on the
-// slice's load mbarrier), issues the four K=16 MMAs of the slice once it
-// has landed and commits them to the slice's MMA mbarrier, which frees the
-// buffer for the slice after next; the load of slice k+1 runs while the
-// tensor core multiplies slice k.  The epilogue reads the accumulator with
+// BF16, one row of a 128-byte swizzle atom) through a ring of kStages
+// shared-memory buffers.  One thread drives the pipeline: it loads slices of
+// A and of B with the tensor memory accelerator (cp.async.bulk.tensor,
+// 128-byte swizzle written by the copy itself, completion counted in bytes
+// on the buffer's load mbarrier) up to kStages ahead -- every slice of the
+// surrogate's K <= 256 at once -- issues the four K=16 MMAs of a slice once
+// it has landed and commits them to the buffer's MMA mbarrier, and refills
+// the buffer of the previous slice once its MMAs are done.  If a bounded
+// wait gives up, every copy and MMA still in flight is waited for (again
+// bounded) before the tensor memory is released and the CTA exits; the
+// output is then left unwritten and the timeout flag set.  The epilogue reads the accumulator with
 // tcgen05.ld (warp w owns tensor-memory lanes 32w..32w+31, i.e. rows
 // 32w..32w+31 of the tile).
 #include <cuda.h>
@@ -27,6 +30,7 @@ namespace {
 
 constexpr int BM = 128;
 constexpr int BK = 64;
+constexpr int kStages = 4;  // shared-memory buffers of K slices
 constexpr int kThreads = 128;
 constexpr int kWaitLimit = 1 << 22;  // try_wait rounds before giving up
 
@@ -156,9 +160,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   constexpr int kStage = stage_bytes<BN>();
   constexpr uint32_t kCols = tmem_cols<BN>();
   constexpr uint32_t kIdesc = idesc_bf16(BM, BN);
-  // bars[0..1]: loads of buffers 0 / 1 landed; bars[2..3]: their MMAs done
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * kStage);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 4);
+  // bars[b]: the load of buffer b landed; bars[kStages + b]: its MMAs done
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages * kStage);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int z = blockIdx.z;
@@ -167,7 +171,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (tid == 0) {
 #pragma unroll
-    for (int i = 0; i < 4; i++) mbar_init(smem_u32(&bars[i]), 1);
+    for (int i = 0; i < 2 * kStages; i++) mbar_init(smem_u32(&bars[i]), 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   if (warp == 0) {
@@ -185,34 +189,54 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int nk = (a.K + BK - 1) / BK;
   bool ok = true;
   if (tid == 0) {
-    int issued = 0;  // slices whose MMAs were committed
-    for (int kt = 0; kt < nk && ok; kt++) {
-      const int s = kt & 1;
-      // the MMAs of slice kt-2 read this buffer: wait for their commit
-      if (kt >= 2 && !mbar_wait(smem_u32(&bars[2 + s]), ((kt - 2) >> 1) & 1)) {
+    // slice kt lives in buffer kt % kStages; its load completes phase
+    // (kt / kStages) & 1 of bars[buffer], its MMAs the same phase of
+    // bars[kStages + buffer]
+    auto load = [&](int kt) {
+      const int b = kt % kStages;
+      const uint32_t ta = smem_u32(smem + b * kStage), tb = ta + kA;
+      mbar_expect_tx(smem_u32(&bars[b]), (uint32_t)kStage);
+      tma_load3(ta, &tmA, kt * BK, m0, za, smem_u32(&bars[b]));
+      tma_load3(tb, &tmB, kt * BK, n0, zb, smem_u32(&bars[b]));
+    };
+    auto phase = [](int kt) { return (uint32_t)((kt / kStages) & 1); };
+    int loaded = 0;     // slices whose loads were issued
+    int landed = 0;     // slices whose loads were seen complete
+    int committed = 0;  // slices whose MMAs were committed
+    int freed = 0;      // slices whose MMAs were seen complete
+    for (; loaded < nk && loaded < kStages; loaded++) load(loaded);
+    for (int kt = 0; kt < nk; kt++) {
+      const int b = kt % kStages;
+      if (!mbar_wait(smem_u32(&bars[b]), phase(kt))) {
         ok = false;
         break;
       }
-      const uint32_t ta = smem_u32(smem + s * kStage), tb = ta + kA;
-      mbar_expect_tx(smem_u32(&bars[s]), (uint32_t)kStage);
-      tma_load3(ta, &tmA, kt * BK, m0, za, smem_u32(&bars[s]));
-      tma_load3(tb, &tmB, kt * BK, n0, zb, smem_u32(&bars[s]));
-      if (!mbar_wait(smem_u32(&bars[s]), (kt >> 1) & 1)) {
-        ok = false;
-        break;
-      }
+      landed = kt + 1;
       tc_fence_after();
+      const uint32_t ta = smem_u32(smem + b * kStage), tb = ta + kA;
 #pragma unroll
       for (int k = 0; k < BK / 16; k++)
         mma_bf16(tmem, sw128_desc(ta + 32 * k), sw128_desc(tb + 32 * k), kIdesc,
                  (kt > 0 || k > 0) ? 1u : 0u);
-      mma_commit(smem_u32(&bars[2 + s]));
-      issued = kt + 1;
+      mma_commit(smem_u32(&bars[kStages + b]));
+      committed = kt + 1;
+      // refill the buffer of the previous slice once its MMAs are done
+      if (kt >= 1 && loaded < nk) {
+        if (!mbar_wait(smem_u32(&bars[kStages + (kt - 1) % kStages]), phase(kt - 1))) {
+          ok = false;
+          break;
+        }
+        freed = kt;
+        load(loaded++);
+      }
     }
-    // every committed slice must have completed before the accumulator is
-    // read or the tensor memory is released: the last commit of each buffer
-    for (int kt = issued > 2 ? issued - 2 : 0; kt < issued; kt++)
-      ok = mbar_wait(smem_u32(&bars[2 + (kt & 1)]), (kt >> 1) & 1) && ok;
+    // Before the accumulator is read, the tensor memory released or the CTA
+    // exits, every copy issued must have landed and every MMA committed must
+    // be done -- also after a timeout above (these waits are bounded too).
+    for (int kt = landed; kt < loaded; kt++)
+      ok = mbar_wait(smem_u32(&bars[kt % kStages]), phase(kt)) && ok;
+    for (int kt = freed > committed - kStages ? freed : committed - kStages; kt < committed; kt++)
+      ok = mbar_wait(smem_u32(&bars[kStages + kt % kStages]), phase(kt)) && ok;
   }
   ok = __syncthreads_and(ok);
   tc_fence_after();
@@ -327,7 +351,7 @@ cudaError_t launch_bn(const GemmArgs& a, int members, cudaStream_t s) {
 }  // namespace
 
 size_t gemm_smem_bytes(int bn) {
-  return 1024 + 2 * (size_t)(BM * BK * 2 + bn * BK * 2) + 64;
+  return 1024 + kStages * (size_t)(BM * BK * 2 + bn * BK * 2) + 16 * kStages + 16;
 }
 
 cudaError_t launch_gemm(const GemmArgs& a, int members, cudaStream_t s) {
