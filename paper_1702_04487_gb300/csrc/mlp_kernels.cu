@@ -242,39 +242,59 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
 
   if (ok) {
+    // Epilogue through shared memory (the operand buffers are free once every
+    // MMA is done): each warp takes its 32 rows x 16 columns from tensor
+    // memory (lane = row), then works row by row -- half-warps on two rows,
+    // lanes along n -- so that bias, aux and every row-major output are read
+    // and written in contiguous runs; the transposed BF16 copy is written
+    // from the lane = row layout, contiguous along m.
+    float* T = reinterpret_cast<float*>(smem) + warp * (32 * 17);
     const int m = m0 + warp * 32 + lane;
     const bool mrow = m < a.M;
     const float* bias = a.bias ? a.bias + z * a.sBias : nullptr;
+    const int jj = lane & 15, rh = lane >> 4;
 #pragma unroll 1
     for (int c0 = 0; c0 < BN; c0 += 16) {
       float v[16];
       tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
       const int nb = n0 + c0;
-      if (nb >= a.N || !mrow) continue;
+      if (nb >= a.N) continue;  // uniform over the CTA
 #pragma unroll
-      for (int j = 0; j < 16; j++) {
-        const int n = nb + j;
-        if (n >= a.N) break;
-        float x = v[j];
+      for (int j = 0; j < 16; j++) T[lane * 17 + j] = v[j];
+      __syncwarp();
+      const int n = nb + jj;
+#pragma unroll 4
+      for (int i = 0; i < 16; i++) {
+        const int r = 2 * i + rh, mm = m0 + warp * 32 + r;
+        if (mm >= a.M || n >= a.N) continue;
+        float x = T[r * 17 + jj];
         if (a.epi == EPI_F32) {
-          a.Cf[z * a.sCf + (size_t)m * a.ldcf + n] = x;
+          a.Cf[z * a.sCf + (size_t)mm * a.ldcf + n] = x;
           continue;
         }
         if (a.epi == EPI_BIAS_F32) {
-          a.Cf[z * a.sCf + (size_t)m * a.ldcf + n] = x + bias[n];
+          a.Cf[z * a.sCf + (size_t)mm * a.ldcf + n] = x + bias[n];
           continue;
         }
         if (a.epi == EPI_BIAS_GELU) {
           x += bias[n];
-          if (a.Zout) a.Zout[z * a.sZ + (size_t)m * a.ldz + n] = x;
+          if (a.Zout) a.Zout[z * a.sZ + (size_t)mm * a.ldz + n] = x;
           x = gelu_f(x);
         } else {  // EPI_GELU_BWD
-          x *= gelu_grad_f(a.aux[z * a.sAux + (size_t)m * a.ldaux + n]);
+          x *= gelu_grad_f(a.aux[z * a.sAux + (size_t)mm * a.ldaux + n]);
         }
         const bf16 hb = __float2bfloat16_rn(x);
-        if (a.Cb) a.Cb[z * a.sCb + (size_t)m * a.ldcb + n] = hb;
-        if (a.Ct) a.Ct[z * a.sCt + (size_t)n * a.ldct + m] = hb;
+        if (a.Cb) a.Cb[z * a.sCb + (size_t)mm * a.ldcb + n] = hb;
+        T[r * 17 + jj] = __bfloat162float(hb);  // for the transposed copy
       }
+      __syncwarp();
+      if (a.Ct && mrow && (a.epi == EPI_BIAS_GELU || a.epi == EPI_GELU_BWD)) {
+#pragma unroll
+        for (int j = 0; j < 16; j++)
+          if (nb + j < a.N)
+            a.Ct[z * a.sCt + (size_t)(nb + j) * a.ldct + m] = __float2bfloat16_rn(T[lane * 17 + j]);
+      }
+      __syncwarp();  // the next chunk overwrites T
     }
   } else if (tid == 0) {
     atomicOr(a.status, kStatusTimeout);
