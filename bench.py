@@ -80,8 +80,8 @@ def device_bytes(p):
     if k == "2d16":
         return c * 30 * 2
     es = 2 if k == "3d16" else 4
-    planes = c // p["nz"] * (p["nz"] + 2)
-    return c * (25 * es + 8) + planes * (25 * es + 4)
+    planes = c // p["nz"] * (p["nz"] + 4)
+    return 2 * c * (25 * es + 4) + 2 * planes * 4
 
 
 def workload(name, rank=0):
@@ -355,9 +355,9 @@ def run_native(args):
 
     if rank == 0:
         peak, peak_kind = measured_peaks()
-        # step-kernel time per time step (2-D: one fused launch per bucket;
-        # 3-D: collide3 + stream3 per lattice), against the algorithmic bytes
-        # of one time step of every lattice
+        # step-kernel time per time step (one fused launch per bucket, every
+        # lattice), against the algorithmic bytes of one time step of every
+        # lattice
         per_step_ms = k_ms / k_steps
         bpl = BYTES_PER_LUP[kind]
         achieved = bpl * cells / (per_step_ms / 1e3) / 1e9
@@ -380,7 +380,7 @@ def run_native(args):
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind
                          if peak_kind == "measured" else "fallback 6.8 TB/s",
-                         "kernel": "step_kernel" if kind in ("2d", "2d16") else "collide3 + stream3",
+                         "kernel": "step_kernel" if kind in ("2d", "2d16") else "step3_kernel",
                          "timed_steps": k_steps, "timed_launches": k_launches,
                          "ms_per_step": per_step_ms, "bytes_per_lup": bpl,
                          "algorithmic_bytes_per_step": bpl * cells},
@@ -550,7 +550,7 @@ def main():
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the default launch shape instead of timing candidates first")
     ap.add_argument("--tune", default="",
-                    help="CHUNK,PREFETCH: fixed launch shape of the 2-D step instead of autotuning")
+                    help="CHUNK,PREFETCH: fixed launch shape instead of autotuning (3-D: z chunk, prefetch 1)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--surrogate", action="store_true",
                     help="measure the surrogate sweep (data generation, training, gated queries)")

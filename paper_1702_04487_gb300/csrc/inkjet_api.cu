@@ -74,6 +74,9 @@ struct ij_handle_s {
   bool odd = false;   // some 2-D lattice has an odd nx (column-by-column copies)
   std::vector<Inst3> inst3;
   Inst3* d_inst3 = nullptr;
+  std::vector<Item3> items3;  // work items of the 3-D step (all lattices)
+  Item3* d_items3 = nullptr;
+  size_t items3_cap = 0;
   float* stage = nullptr;  // FP32 staging of exported / imported states (3-D, 2-D FP16)
   size_t stage_floats = 0;
   std::vector<ij_params> params;
@@ -186,6 +189,8 @@ ij_status validate(const ij_params& p, int k) {
     return fail(IJ_ERR_PARAM, "lattice %d: 2-D FP16 storage needs an even nx", k);
   if (dim == 3) {
     if (p.nz < 1) return fail(IJ_ERR_PARAM, "lattice %d: nz must be >= 1", k);
+    if (p.precision == IJ_FP16_STORE && p.nx % 2 != 0)
+      return fail(IJ_ERR_PARAM, "lattice %d: 3-D FP16 storage needs an even nx", k);
     if (p.nz > 65533 || p.ny > 262140)  // grid limits of the 32 x 4 x 1 blocks
       return fail(IJ_ERR_PARAM, "lattice %d: nz must be <= 65533 and ny <= 262140", k);
     if ((long long)p.nx * p.ny * p.nz > (1LL << 31) / 19)
@@ -524,41 +529,31 @@ ij_status check_handle(ij_handle h) {
   return IJ_OK;
 }
 
-// One 3-D time step on stream s: the collisions of every lattice (with
-// plane sums when diag), the diagnostics record, the streamings.
+// One 3-D time step on stream s (time d_t[0] + t_off): the fused step of
+// every lattice (with plane sums when diag), the wetting ghosts of the new
+// phi, the flip of the current buffers.  The diagnostics record is the
+// caller's.
 cudaError_t enqueue_step3(ij_handle h, cudaStream_t s, int t_off, bool diag, long long* n) {
-  cudaError_t e = cudaSuccess;
-  for (int k = 0; k < h->n_inst && e == cudaSuccess; k++, (*n)++) {
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (h->timing) {
-      e0 = h->get_event();
-      e1 = h->get_event();
-      cudaEventRecord(e0, s);
-    }
-    e = launch_collide3(h->d_inst3, h->inst3[k], k, h->d_t, t_off, diag, s);
-    if (h->timing) {
-      cudaEventRecord(e1, s);
-      h->events.push_back({e0, e1});
-      h->timed_launches++;
-    }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (h->timing) {
+    e0 = h->get_event();
+    e1 = h->get_event();
+    cudaEventRecord(e0, s);
   }
-  if (diag && e == cudaSuccess) {
-    e = launch_finalize(h->d_inst, h->n_inst, h->d_t, s);
-    (*n)++;
+  cudaError_t e = launch_step3(h->d_inst3, h->d_items3, (int)h->items3.size(), h->n_inst, h->d_t,
+                               t_off, diag, h->fp16, s);
+  (*n)++;
+  if (h->timing) {
+    cudaEventRecord(e1, s);
+    h->events.push_back({e0, e1});
+    h->timed_launches++;
   }
-  for (int k = 0; k < h->n_inst && e == cudaSuccess; k++, (*n)++) {
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (h->timing) {
-      e0 = h->get_event();
-      e1 = h->get_event();
-      cudaEventRecord(e0, s);
-    }
-    e = launch_stream3(h->d_inst3, h->inst3[k], k, s);
-    if (h->timing) {
-      cudaEventRecord(e1, s);
-      h->events.push_back({e0, e1});
-    }
-  }
+  if (e != cudaSuccess) return e;
+  e = launch_ghost3(h->d_inst3, h->inst3.data(), h->n_inst, true, s);
+  (*n)++;
+  if (e != cudaSuccess) return e;
+  e = launch_flip3(h->d_inst3, h->n_inst, s);
+  (*n)++;
   return e;
 }
 
@@ -568,6 +563,10 @@ ij_status one_step(ij_handle h) {
     long long n = 0;
     CUDA_TRY(enqueue_step3(h, h->stream, 0, diag, &n));
     h->launches += n;
+    if (diag) {
+      CUDA_TRY(launch_finalize(h->d_inst, h->n_inst, h->d_t, h->stream));
+      h->launches++;
+    }
     CUDA_TRY(launch_advance(h->d_t, 1, h->stream));
     h->launches++;
     h->t++;
@@ -602,9 +601,9 @@ ij_status one_step(ij_handle h) {
 // Capture one diagnostics period into a graph: the step kernels of every
 // bucket with time offsets 0..P-1 (offset 0 with diagnostics when enabled),
 // the record kernel after the first step, and one advance of the time by P.
-// In 2-D the record kernel runs on a branch of its own beside steps 1..P-1:
-// it reads only the FP64 row and lattice sums of step 0 (and resets them)
-// and the time, which those steps do not touch; the branch joins before the
+// The record kernel runs on a branch of its own beside steps 1..P-1: it
+// reads only the FP64 row and lattice sums of step 0 (and resets them) and
+// the time, which those steps do not touch; the branch joins before the
 // advance of the time.
 ij_status build_graph(ij_handle h) {
   h->drop_graph();
@@ -622,13 +621,13 @@ ij_status build_graph(ij_handle h) {
     const bool diag = h->diag_every > 0 && j == 0;
     if (h->is3d) {
       e = enqueue_step3(h, cs, j, diag, &n);
-      continue;
-    }
-    for (const Bucket& b : h->buckets) {
-      e = launch_step(h->d_inst, h->d_items + b.first, b.count, b.nthreads, b.grid, h->d_t, j,
-                      diag, b.prefetch, h->fp16, h->odd, cs);
-      n++;
-      if (e != cudaSuccess) break;
+    } else {
+      for (const Bucket& b : h->buckets) {
+        e = launch_step(h->d_inst, h->d_items + b.first, b.count, b.nthreads, b.grid, h->d_t, j,
+                        diag, b.prefetch, h->fp16, h->odd, cs);
+        n++;
+        if (e != cudaSuccess) break;
+      }
     }
     if (diag && e == cudaSuccess) {
       e = cudaEventRecord(h->ev_fork, cs);
@@ -658,24 +657,66 @@ ij_status build_graph(ij_handle h) {
   return IJ_OK;
 }
 
-// Allocate and initialise the lattices of a 3-D handle.
+// Work items of the 3-D step and their upload (the device array grows only).
+ij_status upload_items3(ij_handle h) {
+  const int n = make_items3(h->inst3.data(), h->n_inst, h->buckets[0].chunk, nullptr);
+  h->items3.resize(n);
+  make_items3(h->inst3.data(), h->n_inst, h->buckets[0].chunk, h->items3.data());
+  if ((size_t)n > h->items3_cap) {
+    h->d_items3 = (Item3*)h->dalloc(n * sizeof(Item3));
+    if (!h->d_items3) return fail(IJ_ERR_OOM, "device allocation of 3-D work items failed");
+    h->items3_cap = n;
+  }
+  Bucket& b = h->buckets[0];
+  b.count = n;
+  CUDA_TRY(cudaMemcpyAsync(h->d_items3, h->items3.data(), n * sizeof(Item3), cudaMemcpyHostToDevice,
+                           h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  h->drop_graph();
+  return IJ_OK;
+}
+
+constexpr int kChunk3Default = 32;  // planes of a 3-D work item before tuning
+
+// Allocate and initialise the lattices of a 3-D handle: per lattice two
+// state buffers (f, g_1..6 in the storage format, g_0 and phi with its
+// wetting ghosts in FP32), the list of ghost cells, the diagnostics over z
+// planes.
 ij_status create3(ij_handle h) {
   const int count = h->n_inst;
   h->is3d = true;
+  for (int k = 1; k < count; k++)
+    if (h->params[k].precision != h->params[0].precision)
+      return fail(IJ_ERR_PARAM, "all 3-D lattices of a batch must share the precision");
+  h->fp16 = h->params[0].precision == IJ_FP16_STORE;
+  cudaError_t e3 = set_step3_smem_limit();
+  if (e3 != cudaSuccess) return fail(IJ_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e3));
   h->inst3.resize(count);
   h->inst.resize(count);
+  std::vector<int> ghosts;
   for (int k = 0; k < count; k++) {
     const ij_params& p = h->params[k];
     Inst3 I = derive3(p);
-    const size_t N = (size_t)p.nx * p.ny * p.nz, NP = (size_t)p.nx * p.ny * (p.nz + 2);
+    const size_t N = (size_t)p.nx * p.ny * p.nz, NE = (size_t)p.nx * p.ny * (p.nz + 4);
     const size_t es = I.fp16 ? 2 : 4;
-    I.f = h->dalloc(19 * N * es);
-    I.g = h->dalloc(6 * N * es);
-    I.g0 = (float*)h->dalloc(N * sizeof(float));
-    I.fp = h->dalloc(std::max(19 * NP * es, N * sizeof(double)));
-    I.gp = h->dalloc(6 * NP * es);
-    I.g0p = (float*)h->dalloc(NP * sizeof(float));
-    I.phi = (float*)h->dalloc(N * sizeof(float));
+    for (int b = 0; b < 2; b++) {
+      // f of one buffer is also the FP64 scratch of the initial phi
+      I.f[b] = h->dalloc(std::max(19 * N * es, N * sizeof(double)));
+      I.g[b] = h->dalloc(6 * N * es);
+      I.g0[b] = (float*)h->dalloc(N * sizeof(float));
+      I.phi[b] = (float*)h->dalloc(NE * sizeof(float));
+      if (!I.f[b] || !I.g[b] || !I.g0[b] || !I.phi[b])
+        return fail(IJ_ERR_OOM, "device allocation of 3-D lattice %d failed", k);
+    }
+    I.n_ghost = ghost_cells3(I, nullptr);
+    ghosts.resize(std::max(1, I.n_ghost));
+    ghost_cells3(I, ghosts.data());
+    I.ghost = (int*)h->dalloc(ghosts.size() * sizeof(int));
+    if (!I.ghost) return fail(IJ_ERR_OOM, "device allocation of 3-D lattice %d failed", k);
+    CUDA_TRY(cudaMemcpyAsync(I.ghost, ghosts.data(), ghosts.size() * sizeof(int),
+                             cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));  // ghosts is reused
+    for (int b = 0; b < 2; b++) CUDA_TRY(cudaMemsetAsync(I.phi[b], 0, NE * sizeof(float), h->stream));
     // diagnostics over z planes, in the 2-D descriptor the record kernel reads
     Inst D;
     memset(&D, 0, sizeof(D));
@@ -689,8 +730,7 @@ ij_status create3(ij_handle h) {
     D.sums = (double*)h->dalloc(4 * sizeof(double));
     D.hist = (double*)h->dalloc((size_t)kHistCap * kRec * sizeof(double));
     D.dstate = (double*)h->dalloc(8 * sizeof(double));
-    if (!I.f || !I.g || !I.g0 || !I.fp || !I.gp || !I.g0p || !I.phi || !D.rows || !D.sums ||
-        !D.hist || !D.dstate)
+    if (!D.rows || !D.sums || !D.hist || !D.dstate)
       return fail(IJ_ERR_OOM, "device allocation of 3-D lattice %d failed", k);
     I.rows = D.rows;
     I.sums = D.sums;
@@ -701,17 +741,28 @@ ij_status create3(ij_handle h) {
   h->d_inst = (Inst*)h->dalloc(count * sizeof(Inst));
   h->d_t = (long long*)h->dalloc(sizeof(long long));
   h->d_status = (unsigned*)h->dalloc(count * sizeof(unsigned));
-  if (!h->d_inst3 || !h->d_inst || !h->d_t || !h->d_status)
+  int* d_cur = (int*)h->dalloc(count * sizeof(int));
+  if (!h->d_inst3 || !h->d_inst || !h->d_t || !h->d_status || !d_cur)
     return fail(IJ_ERR_OOM, "device allocation of descriptors failed");
-  for (int k = 0; k < count; k++) h->inst3[k].status = h->inst[k].status = h->d_status + k;
+  for (int k = 0; k < count; k++) {
+    h->inst3[k].status = h->inst[k].status = h->d_status + k;
+    h->inst3[k].cur = d_cur + k;
+  }
   if (cudaMallocHost((void**)&h->h_status, count * sizeof(unsigned)) != cudaSuccess)
     return fail(IJ_ERR_OOM, "pinned allocation failed");
   memset(h->h_status, 0, count * sizeof(unsigned));
+  int dev = 0, sms = 1;
+  CUDA_TRY(cudaGetDevice(&dev));
+  CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  h->buckets.assign(1, Bucket{kStep3Threads, 0, 0, sms, kChunk3Default, 1});
+  ij_status st = upload_items3(h);
+  if (st != IJ_OK) return st;
   cudaStream_t s = h->stream;
   CUDA_TRY(cudaMemcpyAsync(h->d_inst3, h->inst3.data(), count * sizeof(Inst3), cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaMemcpyAsync(h->d_inst, h->inst.data(), count * sizeof(Inst), cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaMemsetAsync(h->d_t, 0, sizeof(long long), s));
   CUDA_TRY(cudaMemsetAsync(h->d_status, 0, count * sizeof(unsigned), s));
+  CUDA_TRY(cudaMemsetAsync(d_cur, 0, count * sizeof(int), s));
   const double dinit[8] = {0, 0, 0, -1, 0, 0, 0, 0};
   for (int k = 0; k < count; k++) {
     const Inst& D = h->inst[k];
@@ -720,7 +771,7 @@ ij_status create3(ij_handle h) {
     CUDA_TRY(cudaMemsetAsync(D.hist, 0, (size_t)kHistCap * kRec * sizeof(double), s));
     CUDA_TRY(cudaMemcpyAsync(D.dstate, dinit, sizeof(dinit), cudaMemcpyHostToDevice, s));
     CUDA_TRY(launch_init3(h->d_inst3, h->inst3[k], k, s));
-    h->launches += 2;
+    h->launches += 3;
   }
   CUDA_TRY(cudaStreamSynchronize(s));
   return IJ_OK;
@@ -750,8 +801,8 @@ ij_status get_state3(ij_handle h, int index, float* f, float* g, int on_device) 
   return IJ_OK;
 }
 
-// The 3-D state is not double-buffered by time parity, so setting one
-// lattice's time needs no move of the others' state.
+// Each 3-D lattice keeps its own current-buffer index, so setting one
+// lattice's state and time needs no move of the others' state.
 ij_status set_state3(ij_handle h, int index, const float* f, const float* g, long long t,
                      int on_device) {
   const Inst3& J = h->inst3[index];
@@ -1123,7 +1174,14 @@ ij_status ij_kernel_timing(ij_handle h, int enable, double* total_ms, long long*
 ij_status ij_tune(ij_handle h, int block_size, int chunk, int prefetch) {
   ij_status st = check_handle(h);
   if (st != IJ_OK) return st;
-  if (h->is3d) return fail(IJ_ERR_PARAM, "3-D handles have no launch shape to tune");
+  if (h->is3d) {
+    // the z chunk of the 3-D work items; one block size, no prefetch depth
+    if (chunk < 1 || prefetch != 1 || (block_size > 0 && block_size != kStep3Threads))
+      return fail(IJ_ERR_PARAM, "3-D handles take chunk >= 1, prefetch 1, block size %d", kStep3Threads);
+    h->buckets[0].chunk = chunk;
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return upload_items3(h);
+  }
   if (chunk < -5 || prefetch < 1 || prefetch > kMaxPrefetch)
     return fail(IJ_ERR_PARAM, "chunk must be >= -5 and prefetch in 1..%d", kMaxPrefetch);
   bool found = false;
@@ -1142,12 +1200,65 @@ ij_status ij_tune(ij_handle h, int block_size, int chunk, int prefetch) {
   return upload_items(h);
 }
 
+}  // extern "C"
+
+namespace {
+
+// The z chunk of the 3-D work items with the shortest step (trial launches
+// read the state at t and write only the other buffer, without diagnostics
+// or ghosts: the state is unchanged).
+ij_status autotune3(ij_handle h, int reps) {
+  static const int kChunks3[] = {8, 12, 16, 20, 24, 32, 40, 48, 64, 80, 96, 128, 160, 256};
+  int max_nz = 1;
+  for (const Inst3& I : h->inst3) max_nz = std::max(max_nz, I.nz);
+  cudaEvent_t e0, e1;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_chunk = h->buckets[0].chunk;
+  ij_status st = IJ_OK;
+  for (int chunk : kChunks3) {
+    if (chunk > 2 * max_nz) continue;
+    h->buckets[0].chunk = chunk;
+    st = upload_items3(h);
+    if (st != IJ_OK) break;
+    const int n = (int)h->items3.size();
+    cudaError_t e = launch_step3(h->d_inst3, h->d_items3, n, h->n_inst, h->d_t, 0, false, h->fp16,
+                                 h->stream);  // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+    for (int r = 0; r < reps && e == cudaSuccess; r++)
+      e = launch_step3(h->d_inst3, h->d_items3, n, h->n_inst, h->d_t, 0, false, h->fp16, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+      st = fail(IJ_ERR_CUDA, "3-D autotune: %s", cudaGetErrorString(e));
+      break;
+    }
+    h->launches += reps + 1;
+    if (ms < best) {
+      best = ms;
+      best_chunk = chunk;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != IJ_OK) return st;
+  h->buckets[0].chunk = best_chunk;
+  return upload_items3(h);
+}
+
+}  // namespace
+
+extern "C" {
+
 ij_status ij_autotune(ij_handle h, int reps) {
   ij_status st = check_handle(h);
   if (st != IJ_OK) return st;
   if (reps < 1) return fail(IJ_ERR_PARAM, "reps must be >= 1");
   if (h->poisoned) return fail(IJ_ERR_STATE, "handle is poisoned");
-  if (h->is3d) return IJ_OK;  // the 3-D kernels have one fixed launch shape
+  if (h->is3d) return autotune3(h, reps);
   // row chunks, then the cost-balanced variants (chunk <= 0)
   static const int kChunks[] = {8,   16,  24,  32,  40,  48, 56, 64, 72, 80, 88, 96, 104,
                                 112, 120, 128, 160, 192, 256, 0,  -1, -2, -3, -4, -5};

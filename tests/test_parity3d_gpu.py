@@ -226,11 +226,12 @@ def test_small_nozzle3_fp16_error_report(ij, oracle_run3):
     assert rep["phi"] < 0.2 and rep["n"] < 0.05
 
 
-def test_batch3_equals_single(ij):
-    """Two 3-D lattices of different sizes and storage in one handle step
-    exactly as they do alone."""
-    pa = _nozzle()
-    pb = _box(theta_deg=120.0, precision=1)
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch3_equals_single(ij, precision):
+    """Two 3-D lattices of different sizes, geometries and angles in one
+    handle (one launch covers both) step exactly as they do alone."""
+    pa = _nozzle(precision=precision)
+    pb = _box(theta_deg=120.0, precision=precision)
     hb = ij.ij_create([pa, pb])
     ij.ij_step(hb, 40)
     for k, p in enumerate((pa, pb)):
@@ -239,6 +240,13 @@ def test_batch3_equals_single(ij):
         fb, gb = ij.ij_get_state(hb, k)
         fs, gs = ij.ij_get_state(hs, 0)
         assert np.array_equal(fb, fs) and np.array_equal(gb, gs)
+
+
+def test_batch3_rejects_mixed_storage_and_odd_fp16(ij):
+    with pytest.raises(ij.InkjetError):
+        ij.ij_create([_nozzle(), _box(precision=1)])
+    with pytest.raises(ij.InkjetError):
+        ij.ij_create(_box(nx=15, precision=1))
 
 
 def test_graph3_matches_launches(ij):
@@ -272,8 +280,27 @@ def test_numeric_failure3_freezes_one_lattice(ij):
 
 
 def test_tuning_entry_points_on_3d(ij):
-    h = ij.ij_create(_nozzle())
+    """The z chunk of the 3-D work items is the one tunable; any chunk (and
+    the autotuned one) gives bit-identical states."""
+    p = _nozzle(nz=40)
+    ref = ij.ij_create(p)
+    ij.ij_step(ref, 12)
+    fr, gr = ij.ij_get_state(ref, 0)
     with pytest.raises(ij.InkjetError):
-        ij.ij_tune(h, 0, 16, 1)
-    assert ij.ij_autotune(h, 2) == []
-    assert ij.ij_get_tuning(h) == []
+        ij.ij_tune(ref, 0, 16, 2)  # no prefetch depth to tune
+    with pytest.raises(ij.InkjetError):
+        ij.ij_tune(ref, 0, 0, 1)
+    for chunk in (1, 7, 16, 40, 200):
+        h = ij.ij_create(p)
+        ij.ij_tune(h, 0, chunk, 1)
+        (t,) = ij.ij_get_tuning(h)
+        assert t["chunk"] == chunk and t["prefetch"] == 1 and t["block_size"] == 512
+        ij.ij_step(h, 12)
+        f, g = ij.ij_get_state(h, 0)
+        assert np.array_equal(f, fr) and np.array_equal(g, gr), chunk
+    h = ij.ij_create(p)
+    (t,) = ij.ij_autotune(h, 2)
+    assert t["chunk"] >= 1 and t["items"] >= 1
+    ij.ij_step(h, 12)
+    f, g = ij.ij_get_state(h, 0)
+    assert np.array_equal(f, fr) and np.array_equal(g, gr)
