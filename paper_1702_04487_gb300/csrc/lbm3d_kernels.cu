@@ -337,8 +337,12 @@ struct Ctx3 {
   void* gout;
   float* g0out;
   float* phout;
+  // planes; axial boundary; solid planes from the bottom (nozzle length or
+  // plate thickness), which are full planes (plate) or the wall ring; driven
+  // planes below dzl (nozzle length, else all); cells of a plane
+  int nz, bc, zsol, full, dzl, plane;
 };
-static_assert(sizeof(Ctx3) <= 32 * sizeof(float), "Ctx3 outgrew its shared-memory slot");
+static_assert(sizeof(Ctx3) <= 40 * sizeof(float), "Ctx3 outgrew its shared-memory slot");
 
 // Shared memory of one CTA, in words: the staged planes of every warp (two
 // slots), the phi ring (four planes of the tile), the row exchange (two
@@ -350,7 +354,7 @@ struct Smem3 {
   static constexpr int ring = 4 * kW3 * 32;
   static constexpr int xch = 2 * kXch * kW3 * 32;
   static constexpr int diag = 2 * kW3 * 4;
-  static constexpr int ctx = 32;  // the item's Ctx3
+  static constexpr int ctx = 40;  // the item's Ctx3
   static constexpr int words = pops + ring + xch + diag + ctx;
 };
 
@@ -376,12 +380,11 @@ __global__ void __launch_bounds__(kThreads3, 1)
     // a lattice whose numeric flag is set is frozen (uniform over the CTA)
     const bool lead = threadIdx.x == 0;
     if (__syncthreads_or(lead && (*(volatile const unsigned*)I.status & kStatusNumeric))) continue;
-    const int nx = I.nx, ny = I.ny, nz = I.nz;
-    const size_t N = (size_t)nx * ny * nz;
+    const int nx = I.nx, ny = I.ny;
     const int z0 = it.z0, ch = it.ch;
-    const int par = *I.cur;  // buffer of the state at t
     const int xu = it.xs - 2 + lane, yu = it.ys - 2 + w;  // unwrapped column of this thread
     const int x = wrap_any(xu, nx), y = wrap_any(yu, ny);
+    const int cxy = y * nx + x;
     const int xe = min(it.xs + kTile3X, nx), ye = min(it.ys + kTile3Y, ny);
     const bool written = xu >= it.xs && xu < xe && yu >= it.ys && yu < ye;
     // collision results that flow into written cells (the ring of the tile)
@@ -395,15 +398,9 @@ __global__ void __launch_bounds__(kThreads3, 1)
         for (int dx = -1; dx <= 1; dx++)
           if (wall_column3(I, wrap_any(x + dx, nx), wrap_any(y + dy, ny))) wallmask |= 1u << cbit(dx, dy);
     }
-    // solid cells among the nine columns in plane z (extended planes mapped)
-    auto solid_mask = [&](int z) -> unsigned {
-      int zm;
-      if (!map_z(I, z, zm)) return 0x1FFu;
-      if (I.geom == GEOM_NOZZLE) return zm < I.L ? wallmask : 0u;
-      if (I.geom == GEOM_PLATE) return zm < I.wt ? 0x1FFu : 0u;
-      return 0u;
-    };
+    const bool drive_col = I.geom != GEOM_NOZZLE || rr2(I, x, y) < I.R2;
     if (lead) {
+      const int par = *I.cur;  // buffer of the state at t
       CollK3& K = ctx->K;
       K.phis = I.phis;
       K.inv_phis = I.inv_phis;
@@ -426,36 +423,62 @@ __global__ void __launch_bounds__(kThreads3, 1)
       ctx->gout = I.g[par ^ 1];
       ctx->g0out = I.g0[par ^ 1];
       ctx->phout = I.phi[par ^ 1];
+      ctx->nz = I.nz;
+      ctx->bc = I.bc;
+      ctx->zsol = I.geom == GEOM_NOZZLE ? I.L : (I.geom == GEOM_PLATE ? I.wt : 0);
+      ctx->full = I.geom == GEOM_PLATE;
+      ctx->dzl = I.geom == GEOM_NOZZLE ? I.L : 0x7fffffff;
+      ctx->plane = nx * ny;
     }
     __syncthreads();
     const CollK3& K = ctx->K;
-    const bool drive_col = I.geom != GEOM_NOZZLE || rr2(I, x, y) < I.R2;
+    // mapped plane of extended plane z (false: outside a closed domain)
+    auto mapz = [&](int z, int& zm) -> bool {
+      const int nzz = ctx->nz;
+      if ((unsigned)z < (unsigned)nzz) {
+        zm = z;
+        return true;
+      }
+      const int bc = ctx->bc;
+      if (bc == BC_PER) {
+        zm = wrap_any(z, nzz);
+        return true;
+      }
+      zm = z < 0 ? 0 : nzz - 1;
+      return bc == BC_ZG;
+    };
+    // solid cells among the nine columns in mapped plane zm
+    auto solid_of = [&](bool in, int zm) -> unsigned {
+      if (!in) return 0x1FFu;
+      return zm < ctx->zsol ? (ctx->full ? 0x1FFu : wallmask) : 0u;
+    };
+    auto cell_of = [&](int zm) -> size_t { return (size_t)zm * ctx->plane + cxy; };
 
     // Stage the populations of plane zs (its mapped plane) into slot sl, as
     // one cp.async group (FP16: even lanes copy the half pair of their column
     // and the next; nx is even, so pairs never straddle the wrap).
-    auto stage = [&](int zs, int sl, bool need) {
-      int zm;
-      if (need && map_z(I, zs, zm)) {
-        const size_t c = cell3(I, x, y, zm);
+    auto stage = [&](bool in, int zm, int sl, bool need) {
+      if (need && in) {
+        const size_t N = (size_t)ctx->plane * ctx->nz;
+        const size_t c = cell_of(zm);
         const unsigned d = mypop_a + sl * (S::PW * 4);
         if (!H) {
-          const float* f = static_cast<const float*>(ctx->fin);
-          const float* g = static_cast<const float*>(ctx->gin);
+          const float* f = static_cast<const float*>(ctx->fin) + c;
+          const float* g = static_cast<const float*>(ctx->gin) + c;
 #pragma unroll
-          for (int i = 0; i < 19; i++) cp4_async(d + (i * 32 + lane) * 4, f + i * N + c);
+          for (int i = 0; i < 19; i++) cp4_async(d + (i * 32 + lane) * 4, f + i * N);
           cp4_async(d + (19 * 32 + lane) * 4, ctx->g0in + c);
 #pragma unroll
-          for (int i = 0; i < 6; i++) cp4_async(d + ((20 + i) * 32 + lane) * 4, g + i * N + c);
+          for (int i = 0; i < 6; i++) cp4_async(d + ((20 + i) * 32 + lane) * 4, g + i * N);
         } else {
-          const __half* f = static_cast<const __half*>(ctx->fin);
-          const __half* g = static_cast<const __half*>(ctx->gin);
+          const __half* f = static_cast<const __half*>(ctx->fin) + c;
+          const __half* g = static_cast<const __half*>(ctx->gin) + c;
           cp4_async(d + (304 + lane) * 4, ctx->g0in + c);
           if ((lane & 1) == 0) {
 #pragma unroll
-            for (int i = 0; i < 19; i++) cp4_async(d + (i * 16 + (lane >> 1)) * 4, f + i * N + c);
+            for (int i = 0; i < 19; i++) cp4_async(d + (i * 16 + (lane >> 1)) * 4, f + i * N);
 #pragma unroll
-            for (int i = 0; i < 6; i++) cp4_async(d + (336 + i * 16 + (lane >> 1)) * 4, g + i * N + c);
+            for (int i = 0; i < 6; i++) cp4_async(d + (336 + i * 16 + (lane >> 1)) * 4, g + i * N);
           }
         }
       }
@@ -482,10 +505,16 @@ __global__ void __launch_bounds__(kThreads3, 1)
       const int ll = min(31, max(0, lane + dx)), ww = min(kW3 - 1, max(0, w + dy));
       return ring[((((z + 8) & 3) * kW3) + ww) * 32 + ll];
     };
-    auto phi_hat_at = [&](int z) -> float { return ctx->phin[ecell3(I, x, y, z)]; };
+    // phi with wetting ghosts at (x, y, z), z in -2 .. nz + 1
+    auto phi_hat_at = [&](int z) -> float { return ctx->phin[(size_t)(z + 2) * ctx->plane + cxy]; };
 
     // prologue: populations of plane z0 - 1, phi of planes z0 - 2 .. z0
-    stage(z0 - 1, 0, true);
+    // rows 0 and 15 of the CTA give phi to the stencils of rows 1 and 14
+    // only: they stage nothing and do not collide
+    const bool coll = w != 0 && w != kW3 - 1;
+    int zmCur;
+    bool inCur = mapz(z0 - 1, zmCur);
+    stage(inCur, zmCur, 0, coll);
 #pragma unroll
     for (int j = -2; j <= 0; j++) ring[((((z0 + j) + 8) & 3) * kW3 + w) * 32 + lane] = phi_hat_at(z0 + j);
     __syncthreads();
@@ -498,48 +527,60 @@ __global__ void __launch_bounds__(kThreads3, 1)
     float hu5 = 0.f, hu11 = 0.f, hu12 = 0.f, hu15 = 0.f, hu16 = 0.f, hug5 = 0.f;
     float bb11 = 0.f, bb12 = 0.f, bb15 = 0.f, bb16 = 0.f;
     float pg0 = 0.f, pg14 = 0.f, pg5 = 0.f, gs6 = 0.f;
-    unsigned smPrev = solid_mask(z0 - 2);
+    unsigned smPrev, smCur = solid_of(inCur, zmCur);
+    {
+      int zm;
+      const bool in = mapz(z0 - 2, zm);
+      smPrev = solid_of(in, zm);
+    }
+    bool drvCur = drive_col && zmCur < ctx->dzl;
     double sn = 0.0, sphi = 0.0, smom = 0.0;
 #pragma unroll 1
     for (int k = 0; k < ch + 2; k++) {
       const int Zc = z0 - 1 + k;
-      stage(Zc + 1, (k + 1) & 1, k <= ch);
-      const float phn = k <= ch ? phi_hat_at(Zc + 2) : 0.0f;
-      cp_wait3<1>();  // this lane's copies of plane Zc have landed
-      if (H) __syncwarp();  // odd lanes read the half pairs their even neighbour copied
-      const unsigned smCur = solid_mask(Zc);
+      // the next plane: its mapping, staging, solid cells and drive
+      int zmN;
+      const bool inN = mapz(Zc + 1, zmN);
+      stage(inN, zmN, (k + 1) & 1, coll && k <= ch);
+      const float phn = k <= ch ? phi_hat_at(Zc + 2) : 0.0f;  // into the ring before the barrier
+      const unsigned smN = solid_of(inN, zmN);
+      const bool drvN = drive_col && zmN < ctx->dzl;
       const bool fluidC = ((smCur >> cbit(0, 0)) & 1u) == 0u;
-      // ---- collision of (x, y, Zc)
       float fs[19], gP[6], gS[6], g0n, n, uz, u2, phi;
-      {
-        float fr[19], gr[7], nb[19];
-        load_cell(k & 1, fr, gr);
-#pragma unroll
-        for (int i = 0; i < 19; i++) nb[i] = ring_at(Zc + ez3(i), ex3(i), ey3(i));
-        phi = gr[0] + ((gr[1] + gr[2]) + (gr[3] + gr[4]) + (gr[5] + gr[6]));
-        int zm = 0;
-        const bool inz = map_z(I, Zc, zm);
-        const bool driven = drive_col && (I.geom != GEOM_NOZZLE || (inz && zm < I.L));
-        collide3_cell(fr, gr, phi, nb, driven, K, fs, gP, gS, g0n, n, uz, u2);
-      }
-      if (used && fluidC && !(u2 < 0.09f)) atomicOr(I.status, kStatusNumeric);
-      // movers that cross lanes (along x)
-      const float s1 = __shfl_up_sync(kFull, fs[1], 1), s2 = __shfl_down_sync(kFull, fs[2], 1);
-      const float s11 = __shfl_up_sync(kFull, fs[11], 1), s12 = __shfl_down_sync(kFull, fs[12], 1);
-      const float s13 = __shfl_up_sync(kFull, fs[13], 1), s14 = __shfl_down_sync(kFull, fs[14], 1);
-      const float sg1 = __shfl_up_sync(kFull, gP[0], 1), sg2 = __shfl_down_sync(kFull, gP[1], 1);
-      // movers that cross rows (along y), to the exchange: towards y + 1
-      // f_3, f_7, f_8, f_15, f_17, g_3; towards y - 1 f_4, f_9, f_10, f_16,
-      // f_18, g_4
+      float s1, s2, s11, s12, s13, s14, sg1, sg2;
       float* X = xch + (k & 1) * (kXch * kW3 * 32);
-      {
+      if (coll) {
+        cp_wait3<1>();  // this lane's copies of plane Zc have landed
+        if (H) __syncwarp();  // odd lanes read the half pairs their even neighbour copied
+        // ---- collision of (x, y, Zc)
+        {
+          float fr[19], gr[7], nb[19];
+          load_cell(k & 1, fr, gr);
+#pragma unroll
+          for (int i = 0; i < 19; i++) nb[i] = ring_at(Zc + ez3(i), ex3(i), ey3(i));
+          phi = gr[0] + ((gr[1] + gr[2]) + (gr[3] + gr[4]) + (gr[5] + gr[6]));
+          collide3_cell(fr, gr, phi, nb, drvCur, K, fs, gP, gS, g0n, n, uz, u2);
+        }
+        if (used && fluidC && !(u2 < 0.09f)) atomicOr(I.status, kStatusNumeric);
+        // movers that cross lanes (along x)
+        s1 = __shfl_up_sync(kFull, fs[1], 1);
+        s2 = __shfl_down_sync(kFull, fs[2], 1);
+        s11 = __shfl_up_sync(kFull, fs[11], 1);
+        s12 = __shfl_down_sync(kFull, fs[12], 1);
+        s13 = __shfl_up_sync(kFull, fs[13], 1);
+        s14 = __shfl_down_sync(kFull, fs[14], 1);
+        sg1 = __shfl_up_sync(kFull, gP[0], 1);
+        sg2 = __shfl_down_sync(kFull, gP[1], 1);
+        // movers that cross rows (along y), to the exchange: towards y + 1
+        // f_3, f_7, f_8, f_15, f_17, g_3; towards y - 1 f_4, f_9, f_10,
+        // f_16, f_18, g_4
         const float out[kXch] = {fs[3], fs[7], fs[8], fs[15], fs[17], gP[2],
                                  fs[4], fs[9], fs[10], fs[16], fs[18], gP[3]};
 #pragma unroll
         for (int v = 0; v < kXch; v++) X[(v * kW3 + w) * 32 + lane] = out[v];
       }
       ring[((((Zc + 2) + 8) & 3) * kW3 + w) * 32 + lane] = phn;
-      if (DIAG) {
+      if (DIAG && coll) {
         // diagnostics of the state at t: row sums (FP32) of e, e n, e n u_z
         // over the written fluid cells of plane Zc, per warp
         float dg0 = 0.f, dg1 = 0.f, dg2 = 0.f;
@@ -566,98 +607,103 @@ __global__ void __launch_bounds__(kThreads3, 1)
         }
       }
       __syncthreads();
-      if (DIAG && threadIdx.x == 0 && k >= 1 && k <= ch) {
+      if (DIAG && threadIdx.x == 32 && k >= 1 && k <= ch) {
         double s0 = 0.0, s1d = 0.0, s2d = 0.0;
-        for (int ww = 0; ww < kW3; ww++) {
+        for (int ww = 1; ww < kW3 - 1; ww++) {
           const float* D = dsm + ((k & 1) * kW3 + ww) * 4;
           s0 += (double)D[0];
           s1d += (double)D[1];
           s2d += (double)D[2];
         }
+        const int nz = ctx->nz;
         atomicAdd(I.rows + Zc, s0);
         atomicAdd(I.rows + nz + Zc, s1d);
         atomicAdd(I.rows + 2 * nz + Zc, s2d);
       }
-      // incoming movers from the neighbouring rows: (x - c_x, y - c_y)
-      auto xget = [&](int v, int dx, int dy) -> float {
-        const int ll = min(31, max(0, lane + dx)), ww = min(kW3 - 1, max(0, w + dy));
-        return X[(v * kW3 + ww) * 32 + ll];
-      };
-      const float u3 = xget(0, 0, -1), u7 = xget(1, -1, -1), u8 = xget(2, 1, -1);
-      const float u15 = xget(3, 0, -1), u17 = xget(4, 0, -1), ug3 = xget(5, 0, -1);
-      const float d4 = xget(6, 0, 1), d9 = xget(7, -1, 1), d10 = xget(8, 1, 1);
-      const float d16 = xget(9, 0, 1), d18 = xget(10, 0, 1), dg4 = xget(11, 0, 1);
-      // does any cell of the warp have a solid source in planes Zc - 1, Zc
-      const bool any_solid = __any_sync(kFull, (smPrev | smCur) != 0u);
-      auto sol = [](unsigned m, int dx, int dy) { return ((m >> cbit(dx, dy)) & 1u) != 0u; };
-      // ---- plane Zc - 1: the downward movers of plane Zc, then store
-      if (k >= 2) {
-        float f6 = fs[6], f13 = s13, f14 = s14, f17 = u17, f18 = d18, p6 = gP[5];
-        if (any_solid) {
-          if (sol(smCur, 0, 0)) { f6 = hu5; p6 = hug5; }
-          if (sol(smCur, -1, 0)) f13 = bb12;
-          if (sol(smCur, 1, 0)) f14 = bb11;
-          if (sol(smCur, 0, -1)) f17 = bb16;
-          if (sol(smCur, 0, 1)) f18 = bb15;
+      if (coll) {
+        // incoming movers from the neighbouring rows: (x - c_x, y - c_y)
+        auto xget = [&](int v, int dx, int dy) -> float {
+          const int ll = min(31, max(0, lane + dx)), ww = min(kW3 - 1, max(0, w + dy));
+          return X[(v * kW3 + ww) * 32 + ll];
+        };
+        const float u3 = xget(0, 0, -1), u7 = xget(1, -1, -1), u8 = xget(2, 1, -1);
+        const float u15 = xget(3, 0, -1), u17 = xget(4, 0, -1), ug3 = xget(5, 0, -1);
+        const float d4 = xget(6, 0, 1), d9 = xget(7, -1, 1), d10 = xget(8, 1, 1);
+        const float d16 = xget(9, 0, 1), d18 = xget(10, 0, 1), dg4 = xget(11, 0, 1);
+        // does any cell of the warp have a solid source in planes Zc - 1, Zc
+        const bool any_solid = __any_sync(kFull, (smPrev | smCur) != 0u);
+        auto sol = [](unsigned m, int dx, int dy) { return ((m >> cbit(dx, dy)) & 1u) != 0u; };
+        // ---- plane Zc - 1: the downward movers of plane Zc, then store
+        if (k >= 2) {
+          float f6 = fs[6], f13 = s13, f14 = s14, f17 = u17, f18 = d18, p6 = gP[5];
+          if (any_solid) {
+            if (sol(smCur, 0, 0)) { f6 = hu5; p6 = hug5; }
+            if (sol(smCur, -1, 0)) f13 = bb12;
+            if (sol(smCur, 1, 0)) f14 = bb11;
+            if (sol(smCur, 0, -1)) f17 = bb16;
+            if (sol(smCur, 0, 1)) f18 = bb15;
+          }
+          if (written) {
+            const int zo = Zc - 1;
+            const bool sout = sol(smPrev, 0, 0);  // solid cells hold 0
+            const float g6 = sout ? 0.0f : gs6 + p6;
+            const size_t N = (size_t)ctx->plane * ctx->nz, c = cell_of(zo);
+            stS<H>(ctx->fout, 6 * N + c, sout ? 0.0f : f6);
+            stS<H>(ctx->fout, 13 * N + c, sout ? 0.0f : f13);
+            stS<H>(ctx->fout, 14 * N + c, sout ? 0.0f : f14);
+            stS<H>(ctx->fout, 17 * N + c, sout ? 0.0f : f17);
+            stS<H>(ctx->fout, 18 * N + c, sout ? 0.0f : f18);
+            stS<H>(ctx->gout, 5 * N + c, g6);
+            // phi of the new state as the next step sums it (stored values)
+            if (!sout) ctx->phout[c + 2 * (size_t)ctx->plane] = pg0 + (pg14 + (pg5 + stored<H>(g6)));
+          }
         }
-        if (written) {
-          const int zo = Zc - 1;
-          const bool sout = sol(smPrev, 0, 0);  // solid cells hold 0
-          const float g6 = sout ? 0.0f : gs6 + p6;
-          const size_t c = cell3(I, x, y, zo);
-          stS<H>(ctx->fout, 6 * N + c, sout ? 0.0f : f6);
-          stS<H>(ctx->fout, 13 * N + c, sout ? 0.0f : f13);
-          stS<H>(ctx->fout, 14 * N + c, sout ? 0.0f : f14);
-          stS<H>(ctx->fout, 17 * N + c, sout ? 0.0f : f17);
-          stS<H>(ctx->fout, 18 * N + c, sout ? 0.0f : f18);
-          stS<H>(ctx->gout, 5 * N + c, g6);
-          // phi of the new state as the next step sums it (stored values)
-          if (!sout) ctx->phout[ecell3(I, x, y, zo)] = pg0 + (pg14 + (pg5 + stored<H>(g6)));
+        // ---- gather the pulls of plane Zc (rest, in-plane movers, upward
+        // movers of plane Zc - 1, stay parts)
+        {
+          float f1 = s1, f2 = s2, f3 = u3, f4 = d4, f7 = u7, f8 = u8, f9 = d9, f10 = d10;
+          float f5 = hu5, f11 = hu11, f12 = hu12, f15 = hu15, f16 = hu16;
+          float q1 = sg1, q2 = sg2, q3 = ug3, q4 = dg4, q5 = hug5;
+          if (any_solid) {
+            if (sol(smCur, -1, 0)) { f1 = fs[2]; q1 = gP[1]; }
+            if (sol(smCur, 1, 0)) { f2 = fs[1]; q2 = gP[0]; }
+            if (sol(smCur, 0, -1)) { f3 = fs[4]; q3 = gP[3]; }
+            if (sol(smCur, 0, 1)) { f4 = fs[3]; q4 = gP[2]; }
+            if (sol(smCur, -1, -1)) f7 = fs[10];
+            if (sol(smCur, 1, -1)) f8 = fs[9];
+            if (sol(smCur, -1, 1)) f9 = fs[8];
+            if (sol(smCur, 1, 1)) f10 = fs[7];
+            if (sol(smPrev, 0, 0)) { f5 = fs[6]; q5 = gP[5]; }
+            if (sol(smPrev, -1, 0)) f11 = fs[14];
+            if (sol(smPrev, 1, 0)) f12 = fs[13];
+            if (sol(smPrev, 0, -1)) f15 = fs[18];
+            if (sol(smPrev, 0, 1)) f16 = fs[17];
+          }
+          // every pull of plane Zc but f_6, f_13, f_14, f_17, f_18 and the
+          // moving part of g_6 is complete: store it now
+          if (written && k >= 1 && k <= ch) {
+            const bool sc = !fluidC;  // solid cells hold 0
+            const size_t N = (size_t)ctx->plane * ctx->nz, c = cell_of(Zc);
+            const float fo[14] = {fs[0], f1, f2, f3, f4, f5, f7, f8, f9, f10, f11, f12, f15, f16};
+            constexpr int fi[14] = {0, 1, 2, 3, 4, 5, 7, 8, 9, 10, 11, 12, 15, 16};
+  #pragma unroll
+            for (int j = 0; j < 14; j++) stS<H>(ctx->fout, fi[j] * N + c, sc ? 0.0f : fo[j]);
+            const float go[6] = {g0n, gS[0] + q1, gS[1] + q2, gS[2] + q3, gS[3] + q4, gS[4] + q5};
+            ctx->g0out[c] = sc ? 0.0f : go[0];
+  #pragma unroll
+            for (int j = 1; j < 6; j++) stS<H>(ctx->gout, (j - 1) * N + c, sc ? 0.0f : go[j]);
+            pg0 = go[0];
+            pg14 = (stored<H>(go[1]) + stored<H>(go[2])) + (stored<H>(go[3]) + stored<H>(go[4]));
+            pg5 = stored<H>(go[5]);
+            gs6 = gS[5];
+          }
         }
+        hu5 = fs[5]; hu11 = s11; hu12 = s12; hu15 = u15; hu16 = d16; hug5 = gP[4];
+        bb11 = fs[11]; bb12 = fs[12]; bb15 = fs[15]; bb16 = fs[16];
       }
-      // ---- gather the pulls of plane Zc (rest, in-plane movers, upward
-      // movers of plane Zc - 1, stay parts)
-      {
-        float f1 = s1, f2 = s2, f3 = u3, f4 = d4, f7 = u7, f8 = u8, f9 = d9, f10 = d10;
-        float f5 = hu5, f11 = hu11, f12 = hu12, f15 = hu15, f16 = hu16;
-        float q1 = sg1, q2 = sg2, q3 = ug3, q4 = dg4, q5 = hug5;
-        if (any_solid) {
-          if (sol(smCur, -1, 0)) { f1 = fs[2]; q1 = gP[1]; }
-          if (sol(smCur, 1, 0)) { f2 = fs[1]; q2 = gP[0]; }
-          if (sol(smCur, 0, -1)) { f3 = fs[4]; q3 = gP[3]; }
-          if (sol(smCur, 0, 1)) { f4 = fs[3]; q4 = gP[2]; }
-          if (sol(smCur, -1, -1)) f7 = fs[10];
-          if (sol(smCur, 1, -1)) f8 = fs[9];
-          if (sol(smCur, -1, 1)) f9 = fs[8];
-          if (sol(smCur, 1, 1)) f10 = fs[7];
-          if (sol(smPrev, 0, 0)) { f5 = fs[6]; q5 = gP[5]; }
-          if (sol(smPrev, -1, 0)) f11 = fs[14];
-          if (sol(smPrev, 1, 0)) f12 = fs[13];
-          if (sol(smPrev, 0, -1)) f15 = fs[18];
-          if (sol(smPrev, 0, 1)) f16 = fs[17];
-        }
-        // every pull of plane Zc but f_6, f_13, f_14, f_17, f_18 and the
-        // moving part of g_6 is complete: store it now
-        if (written && k >= 1 && k <= ch) {
-          const bool sc = !fluidC;  // solid cells hold 0
-          const size_t c = cell3(I, x, y, Zc);
-          const float fo[14] = {fs[0], f1, f2, f3, f4, f5, f7, f8, f9, f10, f11, f12, f15, f16};
-          constexpr int fi[14] = {0, 1, 2, 3, 4, 5, 7, 8, 9, 10, 11, 12, 15, 16};
-#pragma unroll
-          for (int j = 0; j < 14; j++) stS<H>(ctx->fout, fi[j] * N + c, sc ? 0.0f : fo[j]);
-          const float go[6] = {g0n, gS[0] + q1, gS[1] + q2, gS[2] + q3, gS[3] + q4, gS[4] + q5};
-          ctx->g0out[c] = sc ? 0.0f : go[0];
-#pragma unroll
-          for (int j = 1; j < 6; j++) stS<H>(ctx->gout, (j - 1) * N + c, sc ? 0.0f : go[j]);
-          pg0 = go[0];
-          pg14 = (stored<H>(go[1]) + stored<H>(go[2])) + (stored<H>(go[3]) + stored<H>(go[4]));
-          pg5 = stored<H>(go[5]);
-          gs6 = gS[5];
-        }
-      }
-      hu5 = fs[5]; hu11 = s11; hu12 = s12; hu15 = u15; hu16 = d16; hug5 = gP[4];
-      bb11 = fs[11]; bb12 = fs[12]; bb15 = fs[15]; bb16 = fs[16];
       smPrev = smCur;
+      smCur = smN;
+      drvCur = drvN;
     }
     cp_wait3<0>();  // no copy may land after the CTA moves on
     if (DIAG) {
