@@ -716,7 +716,13 @@ ij_status create3(ij_handle h) {
     CUDA_TRY(cudaMemcpyAsync(I.ghost, ghosts.data(), ghosts.size() * sizeof(int),
                              cudaMemcpyHostToDevice, h->stream));
     CUDA_TRY(cudaStreamSynchronize(h->stream));  // ghosts is reused
-    for (int b = 0; b < 2; b++) CUDA_TRY(cudaMemsetAsync(I.phi[b], 0, NE * sizeof(float), h->stream));
+    // the step never stores solid cells: they hold 0 in both buffers
+    for (int b = 0; b < 2; b++) {
+      CUDA_TRY(cudaMemsetAsync(I.f[b], 0, std::max(19 * N * es, N * sizeof(double)), h->stream));
+      CUDA_TRY(cudaMemsetAsync(I.g[b], 0, 6 * N * es, h->stream));
+      CUDA_TRY(cudaMemsetAsync(I.g0[b], 0, N * sizeof(float), h->stream));
+      CUDA_TRY(cudaMemsetAsync(I.phi[b], 0, NE * sizeof(float), h->stream));
+    }
     // diagnostics over z planes, in the 2-D descriptor the record kernel reads
     Inst D;
     memset(&D, 0, sizeof(D));
@@ -772,6 +778,10 @@ ij_status create3(ij_handle h) {
     CUDA_TRY(cudaMemcpyAsync(D.dstate, dinit, sizeof(dinit), cudaMemcpyHostToDevice, s));
     CUDA_TRY(launch_init3(h->d_inst3, h->inst3[k], k, s));
     h->launches += 3;
+    // the other buffer's f held the FP64 initial phi: clear it again
+    const Inst3& J = h->inst3[k];
+    const size_t N = (size_t)J.nx * J.ny * J.nz;
+    CUDA_TRY(cudaMemsetAsync(J.f[1], 0, std::max(19 * N * (J.fp16 ? 2 : 4), N * sizeof(double)), s));
   }
   CUDA_TRY(cudaStreamSynchronize(s));
   return IJ_OK;

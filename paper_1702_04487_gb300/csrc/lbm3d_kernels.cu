@@ -1,8 +1,8 @@
 // Kernels of the 3-D lift (D3Q19 f, D3Q7 g) of the binary-fluid LBM inkjet
 // step (He et al., arXiv:1702.04487, Eq. 3-10 lifted by moment matching).
 //
-// One time step is one fused launch over every lattice of a handle plus a
-// small one:
+// One time step is one fused launch over every lattice of a handle plus two
+// small ones:
 //  step3:  a CTA of 16 warps holds a 32 (x, lanes) x 16 (y, warps) tile of
 //          columns and marches up z.  Per plane: the populations of the next
 //          plane are staged with cp.async; phi with wetting ghosts comes from
@@ -16,7 +16,8 @@
 //          them collides (its movers enter the tile) or gives phi only.
 //  ghost3: phi of the new state on the solid cells within reach of a fluid
 //          stencil (the wetting ghost values) and on the extended planes of
-//          the axial ends.
+//          the axial ends;
+//  flip3:  the new state becomes current (lattices not frozen).
 // Storage is FP32 or FP16 (f deviations and g_1..6; g_0 FP32); arithmetic
 // is FP32.
 #include <cuda_fp16.h>
@@ -56,6 +57,13 @@ __device__ __forceinline__ float ldS(const void* p, size_t i) {
 }
 template <bool H>
 __device__ __forceinline__ void stS(void* p, size_t i, float v) {
+  if (H)
+    reinterpret_cast<__half*>(p)[i] = __float2half_rn(v);
+  else
+    reinterpret_cast<float*>(p)[i] = v;
+}
+template <bool H>
+__device__ __forceinline__ void stS(void* p, unsigned i, float v) {
   if (H)
     reinterpret_cast<__half*>(p)[i] = __float2half_rn(v);
   else
@@ -365,9 +373,9 @@ __global__ void __launch_bounds__(kThreads3, 1)
   using S = Smem3<H>;
   extern __shared__ float4 smem4[];
   float* const sm = reinterpret_cast<float*>(smem4);
-  float* const ring = sm + S::pops;      // [4][16][32]: phi of plane z in slot (z + 8) & 3
-  float* const xch = ring + S::ring;     // [2][kXch][16][32]
-  float* const dsm = xch + S::xch;       // [2][16][4]
+  float* const ring = sm + S::pops;      // [4][kW3][32]: phi of plane z in slot (z + 8) & 3
+  float* const xch = ring + S::ring;     // [2][kXch][kW3][32]
+  float* const dsm = xch + S::xch;       // [2][kW3][4]
   Ctx3* const ctx = reinterpret_cast<Ctx3*>(dsm + S::diag);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   float* const mypop = sm + w * 2 * S::PW;
@@ -452,33 +460,34 @@ __global__ void __launch_bounds__(kThreads3, 1)
       if (!in) return 0x1FFu;
       return zm < ctx->zsol ? (ctx->full ? 0x1FFu : wallmask) : 0u;
     };
-    auto cell_of = [&](int zm) -> size_t { return (size_t)zm * ctx->plane + cxy; };
+    // cell offsets fit in 32 bits: 19 nx ny nz < 2^31 (checked on the host)
+    auto cell_of = [&](int zm) -> unsigned { return (unsigned)zm * (unsigned)ctx->plane + (unsigned)cxy; };
 
     // Stage the populations of plane zs (its mapped plane) into slot sl, as
     // one cp.async group (FP16: even lanes copy the half pair of their column
     // and the next; nx is even, so pairs never straddle the wrap).
     auto stage = [&](bool in, int zm, int sl, bool need) {
       if (need && in) {
-        const size_t N = (size_t)ctx->plane * ctx->nz;
-        const size_t c = cell_of(zm);
+        const unsigned N = (unsigned)ctx->plane * (unsigned)ctx->nz;
+        const unsigned c = cell_of(zm);
         const unsigned d = mypop_a + sl * (S::PW * 4);
         if (!H) {
-          const float* f = static_cast<const float*>(ctx->fin) + c;
-          const float* g = static_cast<const float*>(ctx->gin) + c;
+          const float* f = static_cast<const float*>(ctx->fin);
+          const float* g = static_cast<const float*>(ctx->gin);
 #pragma unroll
-          for (int i = 0; i < 19; i++) cp4_async(d + (i * 32 + lane) * 4, f + i * N);
+          for (int i = 0; i < 19; i++) cp4_async(d + (i * 32 + lane) * 4, f + (c + i * N));
           cp4_async(d + (19 * 32 + lane) * 4, ctx->g0in + c);
 #pragma unroll
-          for (int i = 0; i < 6; i++) cp4_async(d + ((20 + i) * 32 + lane) * 4, g + i * N);
+          for (int i = 0; i < 6; i++) cp4_async(d + ((20 + i) * 32 + lane) * 4, g + (c + i * N));
         } else {
-          const __half* f = static_cast<const __half*>(ctx->fin) + c;
-          const __half* g = static_cast<const __half*>(ctx->gin) + c;
+          const __half* f = static_cast<const __half*>(ctx->fin);
+          const __half* g = static_cast<const __half*>(ctx->gin);
           cp4_async(d + (304 + lane) * 4, ctx->g0in + c);
           if ((lane & 1) == 0) {
 #pragma unroll
-            for (int i = 0; i < 19; i++) cp4_async(d + (i * 16 + (lane >> 1)) * 4, f + i * N);
+            for (int i = 0; i < 19; i++) cp4_async(d + (i * 16 + (lane >> 1)) * 4, f + (c + i * N));
 #pragma unroll
-            for (int i = 0; i < 6; i++) cp4_async(d + (336 + i * 16 + (lane >> 1)) * 4, g + i * N);
+            for (int i = 0; i < 6; i++) cp4_async(d + (336 + i * 16 + (lane >> 1)) * 4, g + (c + i * N));
           }
         }
       }
@@ -501,16 +510,20 @@ __global__ void __launch_bounds__(kThreads3, 1)
         for (int i = 1; i < 7; i++) gr[i] = __half2float(rh[672 + (i - 1) * 32 + lane]);
       }
     };
+    // phi with ghosts at (x + dx, y + dy, z) from the ring (lanes 0 and 31
+    // read past their row, into the next row, ring plane or region of the
+    // CTA's shared memory; their collisions are not used)
     auto ring_at = [&](int z, int dx, int dy) -> float {
-      const int ll = min(31, max(0, lane + dx)), ww = min(kW3 - 1, max(0, w + dy));
-      return ring[((((z + 8) & 3) * kW3) + ww) * 32 + ll];
+      return ring[((((z + 8) & 3) * kW3) + w + dy) * 32 + lane + dx];
     };
     // phi with wetting ghosts at (x, y, z), z in -2 .. nz + 1
-    auto phi_hat_at = [&](int z) -> float { return ctx->phin[(size_t)(z + 2) * ctx->plane + cxy]; };
+    auto phi_hat_at = [&](int z) -> float {
+      return ctx->phin[(unsigned)(z + 2) * (unsigned)ctx->plane + (unsigned)cxy];
+    };
 
-    // prologue: populations of plane z0 - 1, phi of planes z0 - 2 .. z0
-    // rows 0 and 15 of the CTA give phi to the stencils of rows 1 and 14
-    // only: they stage nothing and do not collide
+    // prologue: populations of plane z0 - 1, phi of planes z0 - 2 .. z0.
+    // The first and last rows of the CTA only give phi to the stencils of
+    // their neighbour rows: they stage nothing and do not collide.
     const bool coll = w != 0 && w != kW3 - 1;
     int zmCur;
     bool inCur = mapz(z0 - 1, zmCur);
@@ -622,10 +635,11 @@ __global__ void __launch_bounds__(kThreads3, 1)
       }
       if (coll) {
         // incoming movers from the neighbouring rows: (x - c_x, y - c_y)
-        auto xget = [&](int v, int dx, int dy) -> float {
-          const int ll = min(31, max(0, lane + dx)), ww = min(kW3 - 1, max(0, w + dy));
-          return X[(v * kW3 + ww) * 32 + ll];
-        };
+        // (lanes 0 and 31 read past their row, the second and second-last
+        // rows read the first and last, which hold no movers: those values
+        // flow only into cells that are not written; every address stays in
+        // the CTA's shared memory)
+        auto xget = [&](int v, int dx, int dy) -> float { return X[(v * kW3 + w + dy) * 32 + lane + dx]; };
         const float u3 = xget(0, 0, -1), u7 = xget(1, -1, -1), u8 = xget(2, 1, -1);
         const float u15 = xget(3, 0, -1), u17 = xget(4, 0, -1), ug3 = xget(5, 0, -1);
         const float d4 = xget(6, 0, 1), d9 = xget(7, -1, 1), d10 = xget(8, 1, 1);
@@ -637,25 +651,27 @@ __global__ void __launch_bounds__(kThreads3, 1)
         if (k >= 2) {
           float f6 = fs[6], f13 = s13, f14 = s14, f17 = u17, f18 = d18, p6 = gP[5];
           if (any_solid) {
-            if (sol(smCur, 0, 0)) { f6 = hu5; p6 = hug5; }
-            if (sol(smCur, -1, 0)) f13 = bb12;
-            if (sol(smCur, 1, 0)) f14 = bb11;
-            if (sol(smCur, 0, -1)) f17 = bb16;
-            if (sol(smCur, 0, 1)) f18 = bb15;
+            const bool s00 = sol(smCur, 0, 0);
+            f6 = s00 ? hu5 : f6;
+            p6 = s00 ? hug5 : p6;
+            f13 = sol(smCur, -1, 0) ? bb12 : f13;
+            f14 = sol(smCur, 1, 0) ? bb11 : f14;
+            f17 = sol(smCur, 0, -1) ? bb16 : f17;
+            f18 = sol(smCur, 0, 1) ? bb15 : f18;
           }
-          if (written) {
+          // solid cells are never stored: both buffers hold 0 there
+          if (written && !sol(smPrev, 0, 0)) {
             const int zo = Zc - 1;
-            const bool sout = sol(smPrev, 0, 0);  // solid cells hold 0
-            const float g6 = sout ? 0.0f : gs6 + p6;
-            const size_t N = (size_t)ctx->plane * ctx->nz, c = cell_of(zo);
-            stS<H>(ctx->fout, 6 * N + c, sout ? 0.0f : f6);
-            stS<H>(ctx->fout, 13 * N + c, sout ? 0.0f : f13);
-            stS<H>(ctx->fout, 14 * N + c, sout ? 0.0f : f14);
-            stS<H>(ctx->fout, 17 * N + c, sout ? 0.0f : f17);
-            stS<H>(ctx->fout, 18 * N + c, sout ? 0.0f : f18);
+            const float g6 = gs6 + p6;
+            const unsigned N = (unsigned)ctx->plane * (unsigned)ctx->nz, c = cell_of(zo);
+            stS<H>(ctx->fout, 6 * N + c, f6);
+            stS<H>(ctx->fout, 13 * N + c, f13);
+            stS<H>(ctx->fout, 14 * N + c, f14);
+            stS<H>(ctx->fout, 17 * N + c, f17);
+            stS<H>(ctx->fout, 18 * N + c, f18);
             stS<H>(ctx->gout, 5 * N + c, g6);
             // phi of the new state as the next step sums it (stored values)
-            if (!sout) ctx->phout[c + 2 * (size_t)ctx->plane] = pg0 + (pg14 + (pg5 + stored<H>(g6)));
+            ctx->phout[c + 2u * (unsigned)ctx->plane] = pg0 + (pg14 + (pg5 + stored<H>(g6)));
           }
         }
         // ---- gather the pulls of plane Zc (rest, in-plane movers, upward
@@ -665,33 +681,39 @@ __global__ void __launch_bounds__(kThreads3, 1)
           float f5 = hu5, f11 = hu11, f12 = hu12, f15 = hu15, f16 = hu16;
           float q1 = sg1, q2 = sg2, q3 = ug3, q4 = dg4, q5 = hug5;
           if (any_solid) {
-            if (sol(smCur, -1, 0)) { f1 = fs[2]; q1 = gP[1]; }
-            if (sol(smCur, 1, 0)) { f2 = fs[1]; q2 = gP[0]; }
-            if (sol(smCur, 0, -1)) { f3 = fs[4]; q3 = gP[3]; }
-            if (sol(smCur, 0, 1)) { f4 = fs[3]; q4 = gP[2]; }
-            if (sol(smCur, -1, -1)) f7 = fs[10];
-            if (sol(smCur, 1, -1)) f8 = fs[9];
-            if (sol(smCur, -1, 1)) f9 = fs[8];
-            if (sol(smCur, 1, 1)) f10 = fs[7];
-            if (sol(smPrev, 0, 0)) { f5 = fs[6]; q5 = gP[5]; }
-            if (sol(smPrev, -1, 0)) f11 = fs[14];
-            if (sol(smPrev, 1, 0)) f12 = fs[13];
-            if (sol(smPrev, 0, -1)) f15 = fs[18];
-            if (sol(smPrev, 0, 1)) f16 = fs[17];
+            const bool cxm = sol(smCur, -1, 0), cxp = sol(smCur, 1, 0);
+            const bool cym = sol(smCur, 0, -1), cyp = sol(smCur, 0, 1), p00 = sol(smPrev, 0, 0);
+            f1 = cxm ? fs[2] : f1;
+            q1 = cxm ? gP[1] : q1;
+            f2 = cxp ? fs[1] : f2;
+            q2 = cxp ? gP[0] : q2;
+            f3 = cym ? fs[4] : f3;
+            q3 = cym ? gP[3] : q3;
+            f4 = cyp ? fs[3] : f4;
+            q4 = cyp ? gP[2] : q4;
+            f7 = sol(smCur, -1, -1) ? fs[10] : f7;
+            f8 = sol(smCur, 1, -1) ? fs[9] : f8;
+            f9 = sol(smCur, -1, 1) ? fs[8] : f9;
+            f10 = sol(smCur, 1, 1) ? fs[7] : f10;
+            f5 = p00 ? fs[6] : f5;
+            q5 = p00 ? gP[5] : q5;
+            f11 = sol(smPrev, -1, 0) ? fs[14] : f11;
+            f12 = sol(smPrev, 1, 0) ? fs[13] : f12;
+            f15 = sol(smPrev, 0, -1) ? fs[18] : f15;
+            f16 = sol(smPrev, 0, 1) ? fs[17] : f16;
           }
           // every pull of plane Zc but f_6, f_13, f_14, f_17, f_18 and the
           // moving part of g_6 is complete: store it now
-          if (written && k >= 1 && k <= ch) {
-            const bool sc = !fluidC;  // solid cells hold 0
-            const size_t N = (size_t)ctx->plane * ctx->nz, c = cell_of(Zc);
+          if (written && k >= 1 && k <= ch && fluidC) {
+            const unsigned N = (unsigned)ctx->plane * (unsigned)ctx->nz, c = cell_of(Zc);
             const float fo[14] = {fs[0], f1, f2, f3, f4, f5, f7, f8, f9, f10, f11, f12, f15, f16};
             constexpr int fi[14] = {0, 1, 2, 3, 4, 5, 7, 8, 9, 10, 11, 12, 15, 16};
-  #pragma unroll
-            for (int j = 0; j < 14; j++) stS<H>(ctx->fout, fi[j] * N + c, sc ? 0.0f : fo[j]);
+#pragma unroll
+            for (int j = 0; j < 14; j++) stS<H>(ctx->fout, fi[j] * N + c, fo[j]);
             const float go[6] = {g0n, gS[0] + q1, gS[1] + q2, gS[2] + q3, gS[3] + q4, gS[4] + q5};
-            ctx->g0out[c] = sc ? 0.0f : go[0];
-  #pragma unroll
-            for (int j = 1; j < 6; j++) stS<H>(ctx->gout, (j - 1) * N + c, sc ? 0.0f : go[j]);
+            ctx->g0out[c] = go[0];
+#pragma unroll
+            for (int j = 1; j < 6; j++) stS<H>(ctx->gout, (j - 1) * N + c, go[j]);
             pg0 = go[0];
             pg14 = (stored<H>(go[1]) + stored<H>(go[2])) + (stored<H>(go[3]) + stored<H>(go[4]));
             pg5 = stored<H>(go[5]);
