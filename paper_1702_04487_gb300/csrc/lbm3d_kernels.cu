@@ -439,7 +439,7 @@ __global__ void __launch_bounds__(kThreads3, 1)
       ctx->plane = nx * ny;
     }
     __syncthreads();
-    const CollK3& K = ctx->K;
+    const CollK3 K = ctx->K;  // in registers for the item
     // mapped plane of extended plane z (false: outside a closed domain)
     auto mapz = [&](int z, int& zm) -> bool {
       const int nzz = ctx->nz;
@@ -548,6 +548,17 @@ __global__ void __launch_bounds__(kThreads3, 1)
     }
     bool drvCur = drive_col && zmCur < ctx->dzl;
     double sn = 0.0, sphi = 0.0, smom = 0.0;
+    // phi at the centre and the four faces (+x, -x, +y, -y) of planes Zc - 1
+    // (pm) and Zc (pc), carried from the iterations that loaded them
+    float pm[5], pc[5];
+    {
+      constexpr int fx[5] = {0, 1, -1, 0, 0}, fy[5] = {0, 0, 0, 1, -1};
+#pragma unroll
+      for (int j = 0; j < 5; j++) {
+        pm[j] = ring_at(z0 - 2, fx[j], fy[j]);
+        pc[j] = ring_at(z0 - 1, fx[j], fy[j]);
+      }
+    }
 #pragma unroll 1
     for (int k = 0; k < ch + 2; k++) {
       const int Zc = z0 - 1 + k;
@@ -569,8 +580,38 @@ __global__ void __launch_bounds__(kThreads3, 1)
         {
           float fr[19], gr[7], nb[19];
           load_cell(k & 1, fr, gr);
+          // D3Q19 neighbours: plane Zc (centre, faces, the four corners),
+          // planes Zc +- 1 (centre and faces)
+          float pn[5];
+          {
+            constexpr int fx[5] = {0, 1, -1, 0, 0}, fy[5] = {0, 0, 0, 1, -1};
 #pragma unroll
-          for (int i = 0; i < 19; i++) nb[i] = ring_at(Zc + ez3(i), ex3(i), ey3(i));
+            for (int j = 0; j < 5; j++) pn[j] = ring_at(Zc + 1, fx[j], fy[j]);
+          }
+          nb[0] = pc[0];
+          nb[1] = pc[1];
+          nb[2] = pc[2];
+          nb[3] = pc[3];
+          nb[4] = pc[4];
+          nb[5] = pn[0];
+          nb[6] = pm[0];
+          nb[7] = ring_at(Zc, 1, 1);
+          nb[8] = ring_at(Zc, -1, 1);
+          nb[9] = ring_at(Zc, 1, -1);
+          nb[10] = ring_at(Zc, -1, -1);
+          nb[11] = pn[1];
+          nb[12] = pn[2];
+          nb[13] = pm[1];
+          nb[14] = pm[2];
+          nb[15] = pn[3];
+          nb[16] = pn[4];
+          nb[17] = pm[3];
+          nb[18] = pm[4];
+#pragma unroll
+          for (int j = 0; j < 5; j++) {
+            pm[j] = pc[j];
+            pc[j] = pn[j];
+          }
           phi = gr[0] + ((gr[1] + gr[2]) + (gr[3] + gr[4]) + (gr[5] + gr[6]));
           collide3_cell(fr, gr, phi, nb, drvCur, K, fs, gP, gS, g0n, n, uz, u2);
         }
