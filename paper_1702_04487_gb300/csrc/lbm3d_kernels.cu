@@ -361,7 +361,7 @@ struct Smem3 {
   static constexpr int pops = kW3 * 2 * PW;
   static constexpr int ring = 4 * kW3 * 32;
   static constexpr int xch = 2 * kXch * kW3 * 32;
-  static constexpr int diag = 2 * kW3 * 4;
+  static constexpr int diag = 2 * kW3 * 8;
   static constexpr int ctx = 40;  // the item's Ctx3
   static constexpr int words = pops + ring + xch + diag + ctx;
 };
@@ -375,7 +375,7 @@ __global__ void __launch_bounds__(kThreads3, 1)
   float* const sm = reinterpret_cast<float*>(smem4);
   float* const ring = sm + S::pops;      // [4][kW3][32]: phi of plane z in slot (z + 8) & 3
   float* const xch = ring + S::ring;     // [2][kXch][kW3][32]
-  float* const dsm = xch + S::xch;       // [2][kW3][4]
+  float* const dsm = xch + S::xch;       // [2][kW3][8]
   Ctx3* const ctx = reinterpret_cast<Ctx3*>(dsm + S::diag);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   float* const mypop = sm + w * 2 * S::PW;
@@ -547,7 +547,7 @@ __global__ void __launch_bounds__(kThreads3, 1)
       smPrev = solid_of(in, zm);
     }
     bool drvCur = drive_col && zmCur < ctx->dzl;
-    double sn = 0.0, sphi = 0.0, smom = 0.0;
+    double sn = 0.0;  // diagnostics: lanes 3, 4, 5 of the first row total n, phi, n u_z
     // phi at the centre and the four faces (+x, -x, +y, -y) of planes Zc - 1
     // (pm) and Zc (pc), carried from the iterations that loaded them
     float pm[5], pc[5];
@@ -635,44 +635,39 @@ __global__ void __launch_bounds__(kThreads3, 1)
       }
       ring[((((Zc + 2) + 8) & 3) * kW3 + w) * 32 + lane] = phn;
       if (DIAG && coll) {
-        // diagnostics of the state at t: row sums (FP32) of e, e n, e n u_z
-        // over the written fluid cells of plane Zc, per warp
-        float dg0 = 0.f, dg1 = 0.f, dg2 = 0.f;
+        // diagnostics of the state at t over the written fluid cells of
+        // plane Zc: the row sums (FP32) of e, e n, e n u_z, n, phi, n u_z
+        float dg[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if (k >= 1 && k <= ch && written && fluidC) {
           const float e = fminf(fmaxf(phi * K.inv_phis, 0.0f), 1.0f);
-          dg0 = e;
-          dg1 = e * n;
-          dg2 = dg1 * uz;
-          sn += (double)n;
-          sphi += (double)phi;
-          smom += (double)(n * uz);
+          dg[0] = e;
+          dg[1] = e * n;
+          dg[2] = dg[1] * uz;
+          dg[3] = n;
+          dg[4] = phi;
+          dg[5] = n * uz;
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          dg0 += __shfl_down_sync(kFull, dg0, o);
-          dg1 += __shfl_down_sync(kFull, dg1, o);
-          dg2 += __shfl_down_sync(kFull, dg2, o);
-        }
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+          for (int j = 0; j < 6; j++) dg[j] += __shfl_down_sync(kFull, dg[j], o);
         if (lane == 0) {
-          float* D = dsm + ((k & 1) * kW3 + w) * 4;
-          D[0] = dg0;
-          D[1] = dg1;
-          D[2] = dg2;
+          float* D = dsm + ((k & 1) * kW3 + w) * 8;
+#pragma unroll
+          for (int j = 0; j < 6; j++) D[j] = dg[j];
         }
       }
       __syncthreads();
-      if (DIAG && threadIdx.x == 32 && k >= 1 && k <= ch) {
-        double s0 = 0.0, s1d = 0.0, s2d = 0.0;
-        for (int ww = 1; ww < kW3 - 1; ww++) {
-          const float* D = dsm + ((k & 1) * kW3 + ww) * 4;
-          s0 += (double)D[0];
-          s1d += (double)D[1];
-          s2d += (double)D[2];
-        }
-        const int nz = ctx->nz;
-        atomicAdd(I.rows + Zc, s0);
-        atomicAdd(I.rows + nz + Zc, s1d);
-        atomicAdd(I.rows + 2 * nz + Zc, s2d);
+      if (DIAG && w == 0 && lane < 6 && k >= 1 && k <= ch) {
+        // the first row (which does not collide): lane j sums value j of the
+        // rows in FP64; plane sums of e, e n, e n u_z, item totals of n,
+        // phi, n u_z
+        double sr = 0.0;
+        for (int ww = 1; ww < kW3 - 1; ww++) sr += (double)dsm[((k & 1) * kW3 + ww) * 8 + lane];
+        if (lane < 3)
+          atomicAdd(I.rows + lane * ctx->nz + Zc, sr);
+        else
+          sn += sr;
       }
       if (coll) {
         // incoming movers from the neighbouring rows: (x - c_x, y - c_y)
@@ -769,19 +764,7 @@ __global__ void __launch_bounds__(kThreads3, 1)
       drvCur = drvN;
     }
     cp_wait3<0>();  // no copy may land after the CTA moves on
-    if (DIAG) {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        sn += __shfl_down_sync(kFull, sn, o);
-        sphi += __shfl_down_sync(kFull, sphi, o);
-        smom += __shfl_down_sync(kFull, smom, o);
-      }
-      if (lane == 0) {
-        atomicAdd(I.sums + 0, sn);
-        atomicAdd(I.sums + 1, sphi);
-        atomicAdd(I.sums + 2, smom);
-      }
-    }
+    if (DIAG && w == 0 && lane >= 3 && lane < 6) atomicAdd(I.sums + (lane - 3), sn);
   }
 }
 
