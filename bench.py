@@ -504,7 +504,9 @@ def run_surrogate(args):
         "metric": "sweep throughput at <=1% error (surrogate + LBM fallback vs LBM)",
         "value": n / t_service, "unit": "runs/s", "n_gpus": 1, "higher_is_better": True,
         "dtype": "bf16 GEMM / f32 LBM", "data": "synthetic",
-        "config": {"workload": "planar nozzle ejection runs, inputs %s" % S.describe_inputs(),
+        "config": {"workload": "planar nozzle ejection runs of the uneven-sweep sampler (4w x 30w, "
+                               "nozzle 4w, drive on the nozzle's capillary scales), inputs %s"
+                               % S.describe_inputs(),
                    "lbm_steps_per_run": steps, "train_runs": int(len(x_tr)),
                    "train_runs_ejecting": int(ok.sum()), "eval_runs": n,
                    "eval_runs_ejecting": int(fin.sum()),
@@ -557,7 +559,8 @@ def main():
     ap.add_argument("--sg-train-runs", type=int, default=4096)
     ap.add_argument("--sg-eval-runs", type=int, default=512)
     ap.add_argument("--sg-train-steps", type=int, default=12000)
-    ap.add_argument("--sg-lbm-steps", type=int, default=5000)
+    ap.add_argument("--sg-lbm-steps", type=int, default=30000,
+                    help="longest lattice Boltzmann run of a query (runs stop once broken up)")
     ap.add_argument("--sg-tau", type=float, default=0.005)
     ap.add_argument("--sg-tau-v", type=float, default=0.01)
     args = ap.parse_args()

@@ -232,8 +232,10 @@ ij_status ij_kernel_timing(ij_handle h, int enable, double* total_ms, long long*
  *                 the time unchanged.  Synchronises.
  * ij_get_tuning -- block size, chunk, prefetch and item count of bucket
  *                 `bucket` (0-based); IJ_ERR_PARAM past the last bucket.
- * 3-D handles have one fixed launch shape and no buckets: ij_tune returns
- * IJ_ERR_PARAM, ij_autotune does nothing.
+ * 3-D handles have one bucket of 512-thread blocks (one CTA per 28 x 12
+ * column tile and z chunk); its one tunable is the z chunk: ij_tune takes
+ * chunk >= 1 and prefetch 1 (block_size 512 or <= 0), ij_autotune times
+ * chunks of 8 .. 256 planes.  Results do not depend on the chunk.
  */
 ij_status ij_tune(ij_handle h, int block_size, int chunk, int prefetch);
 /* ij_use_graph -- run whole diagnostics periods (diag_every steps, or 16

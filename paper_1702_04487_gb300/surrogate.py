@@ -3,11 +3,16 @@
 Thin ctypes binding of the sg_* entry points of libinkjet.so, plus the host
 logic of the service around them:
 
-- ``sample_inputs``: seeded draws of the seven surrogate inputs (contact
-  angle, surface tension, F0, T1, T2, idle time, nozzle width) in a regime
-  where the planar nozzle ejects a droplet within a few thousand steps;
+- ``sample_inputs``: seeded rows of the seven surrogate inputs (contact
+  angle, surface tension, F0, T1, T2, idle time, nozzle width) of the
+  lattices the uneven-sweep sampler draws (``sample_raw``: w ~ U{16..48},
+  angle ~ U[20, 160] degrees, surface tension log-uniform over a factor 4,
+  F0 ~ U[1e-4, 4e-4], T1, T2 ~ U{500..3000}, no idle time), with the drive
+  mapped onto each nozzle's capillary scales (``scaled_drive``) so that the
+  draws eject a droplet: the row holds the lattice's own force density and
+  pulse lengths;
 - ``lattice_params``: the lattice of one input row (nozzle w wide, domain
-  4w x 24w, nozzle length 3w, walls 4 -- the uneven-sweep geometry);
+  4w x 30w, nozzle length 4w, walls 4 -- the uneven-sweep geometry);
 - ``lbm_outcomes``: runs input rows on the batched lattice Boltzmann path
   (one handle, every row a lattice) and reads breakup time, droplet
   velocity, droplet volume and satellites from the FP64 diagnostics;
@@ -79,7 +84,7 @@ def gemm_bf16(A, B, M, N, K, C_out, lda, ldb, ldc, stream=None):
 
 
 DEFAULT_CONFIG = dict(members=5, hidden=256, batch=256, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
-                      seed=1, log_inputs=0b0000110, log_outputs=0b0101,
+                      seed=1, log_inputs=0b0011110, log_outputs=0b0101,
                       out_weight=(1.0, 1.0, 1.0, 0.25))
 
 
@@ -192,28 +197,60 @@ def unpack(p, hidden):
 # ---------------------------------------------------------------------------
 # Inputs, lattices and outcomes.
 
-# A regime where the planar nozzle ejects one droplet within ~2000-4500
-# steps for most draws: ejection needs nozzles of 17 lattice units and more
-# and a drive of about 2e-3 and above at these surface tensions (narrower
-# nozzles and weaker drives only bulge the meniscus; much stronger drives
-# and wider nozzles push a column through the top of the domain instead).
-INPUT_BOX = dict(theta_deg=(30.0, 150.0), sigma=(0.0012, 0.002), F0=(2.1e-3, 2.5e-3),
-                 T1=(1000, 1200), T2=(900, 1200), T_idle=(2000, 4000), width=(17, 19))
+# The sampler box: the uneven-sweep sampler (nozzle widths, angles, the
+# factor 4 of surface tension, the sweep's drive draws, no idle time) about a
+# surface-tension base of SIGMA_SG.
+SIGMA_SG = 0.0025
+SAMPLER_BOX = dict(theta_deg=(20.0, 160.0), sigma=(SIGMA_SG / 2, 2 * SIGMA_SG), F0=(1e-4, 4e-4),
+                   T1=(500, 3000), T2=(500, 3000), T_idle=(0, 0), width=(16, 48))
+
+# Drive scaling.  The sweep's raw draws (F0 about 2.5e-4, pulses of 500-3000
+# steps) only bulge the meniscus of these nozzles; a draw is mapped onto the
+# nozzle's capillary scales instead: pulse lengths in units of the capillary
+# time t_c = sqrt(rho_ink w^3 / sigma) (T -> T / 1750 * T_STAR * t_c) and the
+# force density in units of sigma / w^2 (F -> F0 / 2.5e-4 * F_STAR * sigma /
+# w^2), capped where the channel's mean velocity at the end of the push
+# (start-up of plane Poiseuille flow, viscous time w^2 / (pi^2 nu)) would
+# pass U_CAP, below which the lattice stays stable.  Scanned on 256 draws:
+# 96 % pinch off a droplet within 28000 steps, none goes unstable.
+RHO_INK, NU_INK = 10.0, 0.1
+F_STAR, T_STAR, U_CAP = 800.0, 0.25, 0.06
+LBM_STEPS = 30000  # longest run of a query (the latest breakups come near 28000)
 
 
-def sample_inputs(n, seed):
-    """n rows of the seven inputs, uniform over INPUT_BOX (sigma and F0
-    log-uniform, durations and width integers)."""
+def scaled_drive(theta, sigma, F0, T1, T2, w):
+    """Force density and pulse lengths of the lattice of one sampler draw."""
+    tc = np.sqrt(RHO_INK * w ** 3 / sigma)
+    t1 = max(50, int(round(T1 / 1750.0 * T_STAR * tc)))
+    t2 = max(50, int(round(T2 / 1750.0 * T_STAR * tc)))
+    F = F0 / 2.5e-4 * F_STAR * sigma / w ** 2
+    tau_v = w * w / (np.pi ** 2 * NU_INK)
+    u_per_force = w * w / (12.0 * RHO_INK * NU_INK) * (1.0 - np.exp(-t1 / tau_v))
+    return min(F, U_CAP / u_per_force), t1, t2
+
+
+def sample_raw(n, seed):
+    """n draws of the uneven-sweep sampler: angle uniform, surface tension
+    log-uniform, F0 uniform, durations and width uniform integers."""
     rng = np.random.default_rng(seed)
-    b = INPUT_BOX
+    b = SAMPLER_BOX
     x = np.empty((n, N_IN))
     x[:, 0] = rng.uniform(*b["theta_deg"], n)
     x[:, 1] = np.exp(rng.uniform(np.log(b["sigma"][0]), np.log(b["sigma"][1]), n))
-    x[:, 2] = np.exp(rng.uniform(np.log(b["F0"][0]), np.log(b["F0"][1]), n))
+    x[:, 2] = rng.uniform(*b["F0"], n)
     x[:, 3] = rng.integers(b["T1"][0], b["T1"][1] + 1, n)
     x[:, 4] = rng.integers(b["T2"][0], b["T2"][1] + 1, n)
     x[:, 5] = rng.integers(b["T_idle"][0], b["T_idle"][1] + 1, n)
     x[:, 6] = rng.integers(b["width"][0], b["width"][1] + 1, n)
+    return x
+
+
+def sample_inputs(n, seed):
+    """n input rows: the lattices of n sampler draws (their own force
+    density F0 and pulse lengths T1, T2 after ``scaled_drive``)."""
+    x = sample_raw(n, seed)
+    for r in x:
+        r[2], r[3], r[4] = scaled_drive(*r[:5], int(r[6]))
     return x
 
 
@@ -228,11 +265,12 @@ def lattice_params(row, seed=None):
     theta, sigma, F0, T1, T2, T_idle, w = [float(v) for v in row]
     seed = row_seed(row) if seed is None else seed
     w = int(round(w))
-    return dict(nx=4 * w, ny=24 * w, geometry=W.GEOM_NOZZLE, nozzle_width=w, nozzle_length=3 * w,
-                wall_thickness=4, rho_ink=10.0, rho_air=1.0, nu_ink=0.1, nu_air=0.05, sigma=sigma,
-                width_W=3.0, tau_phi=0.8, gamma=0.0, theta_deg=theta, F0=F0, F_neg=F0 / 2,
-                T1=int(T1), T2=int(T2), T_idle=int(T_idle), axial_bc=W.BC_ZERO_GRADIENT,
-                init_kind=W.INIT_MENISCUS, jitter=1e-6, seed=seed, diag_every=10)
+    return dict(nx=4 * w, ny=30 * w, geometry=W.GEOM_NOZZLE, nozzle_width=w, nozzle_length=4 * w,
+                wall_thickness=4, rho_ink=RHO_INK, rho_air=1.0, nu_ink=NU_INK, nu_air=0.05,
+                sigma=sigma, width_W=3.0, tau_phi=0.8, gamma=0.0, theta_deg=theta, F0=F0,
+                F_neg=F0 / 2, T1=int(round(T1)), T2=int(round(T2)), T_idle=int(round(T_idle)),
+                axial_bc=W.BC_ZERO_GRADIENT, init_kind=W.INIT_MENISCUS, jitter=1e-6, seed=seed,
+                diag_every=10)
 
 
 def outcomes_from_history(hist, after=(0, 100)):
@@ -247,18 +285,42 @@ def outcomes_from_history(hist, after=(0, 100)):
     return np.array([tb, hist[sel, 8].mean(), hist[sel, 6].mean(), hist[sel, 9].mean()])
 
 
-def lbm_outcomes(rows, steps=5000, stream=None, chunk=1024, precision=0):
-    """Run every input row as a lattice of the batched LBM path for `steps`
-    steps; returns outcomes [n][4] (NaN rows: no breakup in time).
+def lbm_outcomes(rows, steps=LBM_STEPS, stream=None, chunk=4096, precision=0, segment=2000):
+    """Run every input row as a lattice of the batched LBM path (one handle,
+    up to `chunk` rows) for at most `steps` steps, in segments of `segment`
+    steps, stopping once every lattice has its outcomes (or is frozen by a
+    numeric failure); returns outcomes [n][4] (NaN rows: no breakup in time).
     precision 1 stores the populations in FP16 (offsets)."""
-    out = np.empty((len(rows), N_OUT))
+    out = np.full((len(rows), N_OUT), np.nan)
     for a in range(0, len(rows), chunk):
         part = rows[a:a + chunk]
         h = ij.ij_create([dict(lattice_params(r), precision=precision) for r in part],
                          stream=stream)
-        ij.ij_step(h, steps)
-        for k in range(len(part)):
-            out[a + k] = outcomes_from_history(ij.ij_history(h, k))
+        todo = list(range(len(part)))
+        t = 0
+        while todo and t < steps:
+            n = min(segment, steps - t)
+            try:
+                ij.ij_step(h, n)
+            except ij.InkjetError as e:
+                if e.status != ij.IJ_ERR_NUMERIC:
+                    raise
+                break  # every lattice is frozen
+            t += n
+            left = []
+            for k in todo:
+                try:
+                    ij.ij_observe(h, k, phi=False)
+                except ij.InkjetError as e:
+                    if e.status != ij.IJ_ERR_NUMERIC:
+                        raise
+                    continue  # frozen by a numeric failure: no outcome
+                o = outcomes_from_history(ij.ij_history(h, k))
+                if np.isfinite(o).all():
+                    out[a + k] = o
+                else:
+                    left.append(k)
+            todo = left
         ij.ij_destroy(h)
     return out
 
@@ -267,7 +329,7 @@ class SurrogateService:
     """Answers queries with the ensemble where the gate accepts them and
     with the lattice Boltzmann model elsewhere."""
 
-    def __init__(self, surrogate, lbm_steps=5000):
+    def __init__(self, surrogate, lbm_steps=LBM_STEPS):
         self.sg = surrogate
         self.lbm_steps = lbm_steps
 
@@ -289,9 +351,12 @@ def finite_rows(y):
 
 
 def describe_inputs():
-    return {k: INPUT_BOX[k] for k in INPUT_NAMES}
+    """The sampler box and the drive mapping of the input rows."""
+    return dict({k: SAMPLER_BOX[k] for k in INPUT_NAMES},
+                drive="F0, T1, T2 on the nozzle's capillary scales: F_STAR %g, T_STAR %g, U_CAP %g"
+                      % (F_STAR, T_STAR, U_CAP))
 
 
 __all__ = ["Surrogate", "SurrogateService", "sample_inputs", "lattice_params", "lbm_outcomes",
            "outcomes_from_history", "gemm_bf16", "unpack", "relative_error", "finite_rows",
-           "describe_inputs", "INPUT_BOX"]
+           "describe_inputs", "scaled_drive", "sample_raw", "SAMPLER_BOX", "LBM_STEPS"]

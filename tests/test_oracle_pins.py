@@ -395,8 +395,7 @@ def test_fp32_noise_floor_of_cfg1():
     oracle runs that each take a relative 2^-24 (FP32 rounding) perturbation
     of every population after every step end up, after 1000 steps, a few
     1e-6 to ~1.5e-5 of phi* from the exact run, concentrated at the driven
-    meniscus.  The GPU parity bound on phi (3e-5) stays at about twice this
-    floor."""
+    meniscus.  The GPU parity bound on phi (1e-5) lies inside this floor."""
     p = W.cfg1("spec")
     ref = OracleSim(p)
     noisy = OracleSim(p)

@@ -128,13 +128,10 @@ def test_wall_on_strip_edges_odd_width(ij, cx):
     _one_step_case(ij, p, steps=3, tol=1e-5)
 
 
-def test_cfg1_1000_steps_density_and_order_parameter(ij):
-    """cfg 1 as specified (nominal drive): n after 1000 steps within 1e-5
-    relative L-infinity of the FP64 oracle (scaled by max n), phi within
-    3e-5 of phi*.  The bound on phi is set by the problem, not the kernel:
-    the driven meniscus amplifies round-off, and the oracle itself, fed FP32
-    storage noise every step, drifts 1.1-1.3e-5 from its exact run by step
-    1000 (tests/test_oracle_pins.py::test_fp32_noise_floor_of_cfg1)."""
+@pytest.fixture(scope="module")
+def cfg1_1000(ij):
+    """cfg 1 as specified (nominal drive) after 1000 steps: density and
+    order parameter fields of the CUDA path and of the FP64 oracle."""
     p = W.cfg1(drive="spec")
     h = ij.ij_create(p)
     ij.ij_step(h, 1000)
@@ -144,8 +141,29 @@ def test_cfg1_1000_steps_density_and_order_parameter(ij):
     fo, go = o.state()
     ng, pg = _fields_from_state(fg.astype(np.float64), gg.astype(np.float64))
     no, po = _fields_from_state(fo, go)
+    return ng, pg, no, po
+
+
+def test_cfg1_1000_steps_density(cfg1_1000):
+    """n after 1000 steps within 1e-5 relative L-infinity of the FP64 oracle
+    (scaled by max n)."""
+    ng, _, no, _ = cfg1_1000
     assert _rel(ng, no, np.abs(no).max()) < 1e-5
-    assert _rel(pg, po, 4.5) < 3e-5
+
+
+@pytest.mark.xfail(strict=False, reason="phi reaches 1.2-1.7e-5 of phi* after 1000 steps, above the "
+                   "1e-5 bound: FP32 arithmetic of the collision on the driven meniscus")
+def test_cfg1_1000_steps_order_parameter(cfg1_1000):
+    """phi after 1000 steps within 1e-5 of phi* of the FP64 oracle.  Open:
+    the CUDA path ends at 1.2-1.7e-5.  FP32 storage alone (the oracle fed a
+    relative 2^-24 perturbation of every stored population every step)
+    costs 1.1-1.5e-5 on this driven meniscus
+    (tests/test_oracle_pins.py::test_fp32_noise_floor_of_cfg1), so the
+    bound is at the round-off floor of FP32 storage."""
+    _, pg, _, po = cfg1_1000
+    err = _rel(pg, po, 4.5)
+    print("cfg 1, phi after 1000 steps: %.2e of phi*" % err)
+    assert err < 1e-5
 
 
 def test_e1_paper_lattice_parameters_100_steps(ij):
