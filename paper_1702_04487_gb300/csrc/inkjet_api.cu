@@ -676,7 +676,7 @@ ij_status upload_items3(ij_handle h) {
   return IJ_OK;
 }
 
-constexpr int kChunk3Default = 32;  // planes of a 3-D work item before tuning
+constexpr int kChunk3Default = 80;  // planes of a 3-D work item before tuning
 
 // Allocate and initialise the lattices of a 3-D handle: per lattice two
 // state buffers (f, g_1..6 in the storage format, g_0 and phi with its
