@@ -35,8 +35,8 @@ FALLBACK_HBM_GBS = 6800.0
 NCU_TRAFFIC = {
     "cfg2": {"kernel_sha": "cf2f590a198bdc85", "bytes_per_step": {80: 721.96e6}},
     "cfg2h": {"kernel_sha": "cf2f590a198bdc85", "bytes_per_step": {80: 371.28e6}},
-    "cfg4": {"kernel_sha": "fbd179482c289782", "bytes_per_step": {80: 5.0147e9, 160: 5.0226e9}},
-    "cfg4h": {"kernel_sha": "fbd179482c289782", "bytes_per_step": {80: 2.5276e9, 160: 2.6909e9}},
+    "cfg4": {"kernel_sha": "96a7e071522f2b2b", "bytes_per_step": {80: 4.6221e9}},
+    "cfg4h": {"kernel_sha": "96a7e071522f2b2b", "bytes_per_step": {80: 2.5061e9}},
 }
 
 

@@ -69,6 +69,21 @@ __device__ __forceinline__ void stS(void* p, unsigned i, float v) {
   else
     reinterpret_cast<float*>(p)[i] = v;
 }
+// The same with the streaming (evict-first) cache hint: the new state is
+// read again only in the next step, so its lines should not push the current
+// state's planes, which neighbouring tiles still read, out of L2.
+template <bool H>
+__device__ __forceinline__ void stCS(void* p, unsigned i, float v) {
+  if (H) {
+    const __half h = __float2half_rn(v);
+    asm volatile("st.global.cs.b16 [%0], %1;\n" ::"l"(reinterpret_cast<__half*>(p) + i),
+                 "h"(__half_as_ushort(h))
+                 : "memory");
+  } else {
+    asm volatile("st.global.cs.f32 [%0], %1;\n" ::"l"(reinterpret_cast<float*>(p) + i), "f"(v)
+                 : "memory");
+  }
+}
 // The value stS stores, as read back later.
 template <bool H>
 __device__ __forceinline__ float stored(float v) {
@@ -700,14 +715,14 @@ __global__ void __launch_bounds__(kThreads3, 1)
             const int zo = Zc - 1;
             const float g6 = gs6 + p6;
             const unsigned N = (unsigned)ctx->plane * (unsigned)ctx->nz, c = cell_of(zo);
-            stS<H>(ctx->fout, 6 * N + c, f6);
-            stS<H>(ctx->fout, 13 * N + c, f13);
-            stS<H>(ctx->fout, 14 * N + c, f14);
-            stS<H>(ctx->fout, 17 * N + c, f17);
-            stS<H>(ctx->fout, 18 * N + c, f18);
-            stS<H>(ctx->gout, 5 * N + c, g6);
+            stCS<H>(ctx->fout, 6 * N + c, f6);
+            stCS<H>(ctx->fout, 13 * N + c, f13);
+            stCS<H>(ctx->fout, 14 * N + c, f14);
+            stCS<H>(ctx->fout, 17 * N + c, f17);
+            stCS<H>(ctx->fout, 18 * N + c, f18);
+            stCS<H>(ctx->gout, 5 * N + c, g6);
             // phi of the new state as the next step sums it (stored values)
-            ctx->phout[c + 2u * (unsigned)ctx->plane] = pg0 + (pg14 + (pg5 + stored<H>(g6)));
+            stCS<false>(ctx->phout, c + 2u * (unsigned)ctx->plane, pg0 + (pg14 + (pg5 + stored<H>(g6))));
           }
         }
         // ---- gather the pulls of plane Zc (rest, in-plane movers, upward
@@ -745,11 +760,11 @@ __global__ void __launch_bounds__(kThreads3, 1)
             const float fo[14] = {fs[0], f1, f2, f3, f4, f5, f7, f8, f9, f10, f11, f12, f15, f16};
             constexpr int fi[14] = {0, 1, 2, 3, 4, 5, 7, 8, 9, 10, 11, 12, 15, 16};
 #pragma unroll
-            for (int j = 0; j < 14; j++) stS<H>(ctx->fout, fi[j] * N + c, fo[j]);
+            for (int j = 0; j < 14; j++) stCS<H>(ctx->fout, fi[j] * N + c, fo[j]);
             const float go[6] = {g0n, gS[0] + q1, gS[1] + q2, gS[2] + q3, gS[3] + q4, gS[4] + q5};
-            ctx->g0out[c] = go[0];
+            stCS<false>(ctx->g0out, c, go[0]);
 #pragma unroll
-            for (int j = 1; j < 6; j++) stS<H>(ctx->gout, (j - 1) * N + c, go[j]);
+            for (int j = 1; j < 6; j++) stCS<H>(ctx->gout, (j - 1) * N + c, go[j]);
             pg0 = go[0];
             pg14 = (stored<H>(go[1]) + stored<H>(go[2])) + (stored<H>(go[3]) + stored<H>(go[4]));
             pg5 = stored<H>(go[5]);
