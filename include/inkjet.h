@@ -16,11 +16,15 @@
  * is z.  Their populations are f[i][z][y][x] (i = 0..18) and g[i][z][y][x]
  * (i = 0..6): rest, +x, -x, +y, -y, +z, -z, then the 12 edge directions
  * (+x+y, -x+y, +x-y, -x-y, +x+z, -x+z, +x-z, -x-z, +y+z, -y+z, +y-z, -y-z).
- * Each step is two launches per lattice (collision, then streaming) over a
- * post-collision copy of the populations; the diagnostics below then run
- * over z planes (w(z) = sum over x, y of e; mom_y is the sum of n u_z; the
- * neck criterion needs more than pi R^2 of run ink above).  All lattices of
- * a handle have the same dim.
+ * Each step is one fused launch over every lattice of the handle (a CTA per
+ * 28 x 12 column tile and z chunk marches up z, streaming in push form),
+ * then the wetting ghosts of the new phi; the state is double-buffered per
+ * lattice, and a lattice frozen by a numeric failure keeps its last good
+ * state.  All 3-D lattices of a handle share the storage format (FP16
+ * storage needs an even nx).  The diagnostics below run over z planes
+ * (w(z) = sum over x, y of e; mom_y is the sum of n u_z; the neck criterion
+ * needs more than pi R^2 of run ink above).  All lattices of a handle have
+ * the same dim.
  *
  * Conventions for every entry point:
  *  - All quantities are lattice units (delta x = delta t = 1).
