@@ -50,6 +50,9 @@ typedef struct {
   int log_inputs;          /* bit d set: input d is log-transformed before z-scoring */
   int log_outputs;         /* bit d set: outcome d likewise */
   float out_weight[4];     /* loss weight of each outcome */
+  int lr_cosine;           /* 1: within each sg_train call lr decays from lr to 0 along a
+                              half cosine, lr (1 + cos(pi s / S)) / 2 at step s of S;
+                              0: constant lr */
 } sg_config;
 
 /* sg_create -- allocate an ensemble and initialise it: He-uniform weights
@@ -67,7 +70,8 @@ ij_status sg_create(const sg_config* cfg, ij_alloc_fn alloc, ij_free_fn free_fn,
 ij_status sg_set_data(sg_handle h, const float* x, const float* y, int n);
 
 /* sg_train -- `steps` Adam steps of every member, each on its own minibatch
- * of `batch` rows drawn with replacement.  *loss (may be NULL) receives the
+ * of `batch` rows drawn with replacement (lr constant, or decaying over these
+ * steps with lr_cosine).  *loss (may be NULL) receives the
  * mean over members of the last step's loss.  Synchronises. */
 ij_status sg_train(sg_handle h, int steps, double* loss);
 

@@ -93,9 +93,14 @@ struct Layout {
 };
 // Adam (bias-corrected, step t = *d_step + 1) on every parameter of every
 // member, then BF16 copies: Wb (same layout) and WbT (layer-wise transposes).
+// d_sched (may be null): {first step, step count} of the current training
+// call, over which lr decays along a half cosine.
 cudaError_t launch_adam(float* p, const float* g, float* m, float* v, const Layout& L, int members,
                         float lr, float beta1, float beta2, float eps, const long long* d_step,
-                        bf16* Wb, bf16* WbT, cudaStream_t s);
+                        const long long* d_sched, bf16* Wb, bf16* WbT, cudaStream_t s);
+// d_sched = {*d_step, steps}: the start of a training call of `steps` steps.
+cudaError_t launch_schedule_begin(const long long* d_step, long long* d_sched, long long steps,
+                                  cudaStream_t s);
 // BF16 copies of the parameters without an update.
 cudaError_t launch_cast_params(const float* p, const Layout& L, int members, bf16* Wb, bf16* WbT,
                                cudaStream_t s);

@@ -524,12 +524,20 @@ __device__ __forceinline__ void locate(const Layout& L, long long i, int& l, int
   }
 }
 
+// d_sched (may be null): {first step, number of steps} of the current
+// training call; lr then decays along a half cosine, lr (1 + cos(pi s / S)) / 2
+// at its step s of S.
 __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
                             float* __restrict__ v, const Layout L, int members, float lr,
                             float beta1, float beta2, float eps, const long long* __restrict__ d_step,
-                            bf16* __restrict__ Wb, bf16* __restrict__ WbT) {
+                            const long long* __restrict__ d_sched, bf16* __restrict__ Wb,
+                            bf16* __restrict__ WbT) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= L.total * members) return;
+  if (d_sched && d_sched[1] > 0) {
+    const float frac = (float)(*d_step - d_sched[0]) / (float)d_sched[1];
+    lr *= 0.5f * (1.0f + cospif(fminf(fmaxf(frac, 0.0f), 1.0f)));
+  }
   const float t = (float)(*d_step + 1);
   const float bc1 = 1.0f - powf(beta1, t), bc2 = 1.0f - powf(beta2, t);
   const float gi = g[i];
@@ -683,9 +691,21 @@ cudaError_t launch_rowsum_f32(const float* in, int rows, int cols, int ld, long 
 
 cudaError_t launch_adam(float* p, const float* g, float* m, float* v, const Layout& L, int members,
                         float lr, float beta1, float beta2, float eps, const long long* d_step,
-                        bf16* Wb, bf16* WbT, cudaStream_t s) {
+                        const long long* d_sched, bf16* Wb, bf16* WbT, cudaStream_t s) {
   adam_kernel<<<blocks(L.total * members, 256), 256, 0, s>>>(p, g, m, v, L, members, lr, beta1,
-                                                              beta2, eps, d_step, Wb, WbT);
+                                                              beta2, eps, d_step, d_sched, Wb, WbT);
+  return cudaGetLastError();
+}
+
+__global__ void schedule_begin_kernel(const long long* __restrict__ d_step, long long* d_sched,
+                                      long long steps) {
+  d_sched[0] = *d_step;
+  d_sched[1] = steps;
+}
+
+cudaError_t launch_schedule_begin(const long long* d_step, long long* d_sched, long long steps,
+                                  cudaStream_t s) {
+  schedule_begin_kernel<<<1, 1, 0, s>>>(d_step, d_sched, steps);
   return cudaGetLastError();
 }
 

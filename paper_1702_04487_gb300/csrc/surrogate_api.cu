@@ -76,6 +76,7 @@ struct sg_handle_s {
   double* d_loss = nullptr;
   unsigned* d_status = nullptr;
   long long* d_step = nullptr;
+  long long* d_sched = nullptr;  // {first step, steps} of the current sg_train call
   cudaStream_t cap = nullptr;
   cudaGraphExec_t gexec = nullptr;
   // inference workspace (grown on demand)
@@ -305,7 +306,8 @@ cudaError_t enqueue_train_step(sg_handle h, cudaStream_t s) {
   if (e == cudaSuccess) e = enqueue_backward(h, h->bm, s);
   if (e == cudaSuccess)
     e = launch_adam(h->p, h->g, h->m, h->v, h->L, h->K, h->cfg.lr, h->cfg.beta1, h->cfg.beta2,
-                    h->cfg.eps, h->d_step, h->Wb, h->WbT, s);
+                    h->cfg.eps, h->d_step, h->cfg.lr_cosine ? h->d_sched : nullptr, h->Wb, h->WbT,
+                    s);
   if (e == cudaSuccess) e = launch_advance_step(h->d_step, s);
   return e;
 }
@@ -369,6 +371,7 @@ ij_status sg_create(const sg_config* cfg, ij_alloc_fn alloc, ij_free_fn free_fn,
   if (!(cfg->lr > 0) || !(cfg->beta1 >= 0 && cfg->beta1 < 1) || !(cfg->beta2 >= 0 && cfg->beta2 < 1) ||
       !(cfg->eps > 0))
     return fail(IJ_ERR_PARAM, "Adam settings out of range");
+  if (cfg->lr_cosine != 0 && cfg->lr_cosine != 1) return fail(IJ_ERR_PARAM, "lr_cosine must be 0 or 1");
   sg_handle h = new sg_handle_s();
   h->cfg = *cfg;
   h->K = cfg->members;
@@ -410,13 +413,15 @@ ij_status sg_create(const sg_config* cfg, ij_alloc_fn alloc, ij_free_fn free_fn,
   h->d_loss = (double*)h->dalloc(K * 8);
   h->d_status = (unsigned*)h->dalloc(4);
   h->d_step = (long long*)h->dalloc(8);
+  h->d_sched = (long long*)h->dalloc(16);
   h->d_lo = (float*)h->dalloc(kIn * 4);
   h->d_hi = (float*)h->dalloc(kIn * 4);
   h->d_w = (float*)h->dalloc(kOut * 4);
   for (void* b : {(void*)h->p, (void*)h->g, (void*)h->m, (void*)h->v, (void*)h->Wb, (void*)h->WbT,
                   (void*)h->Xb, (void*)h->Xbt, (void*)h->Tb, (void*)h->Y, (void*)h->dY,
                   (void*)h->dYt, (void*)h->dYft, (void*)h->d_loss, (void*)h->d_status,
-                  (void*)h->d_step, (void*)h->d_lo, (void*)h->d_hi, (void*)h->d_w})
+                  (void*)h->d_step, (void*)h->d_sched, (void*)h->d_lo, (void*)h->d_hi,
+                  (void*)h->d_w})
     if (!b) return bail(fail(IJ_ERR_OOM, "device allocation failed"));
   for (int l = 0; l < kHidden; l++)
     if (!h->Z[l] || !h->Ha[l] || !h->Ht[l]) return bail(fail(IJ_ERR_OOM, "device allocation failed"));
@@ -445,6 +450,7 @@ ij_status sg_create(const sg_config* cfg, ij_alloc_fn alloc, ij_free_fn free_fn,
   CUDA_TRY(cudaMemsetAsync(h->v, 0, KP * 4, s));
   CUDA_TRY(cudaMemsetAsync(h->d_status, 0, 4, s));
   CUDA_TRY(cudaMemsetAsync(h->d_step, 0, 8, s));
+  CUDA_TRY(cudaMemsetAsync(h->d_sched, 0, 16, s));
   CUDA_TRY(cudaMemcpyAsync(h->d_w, cfg->out_weight, kOut * 4, cudaMemcpyHostToDevice, s));
   CUDA_TRY(launch_cast_params(h->p, h->L, h->K, h->Wb, h->WbT, s));
   CUDA_TRY(cudaStreamSynchronize(s));
@@ -540,6 +546,8 @@ ij_status sg_train(sg_handle h, int steps, double* loss) {
     cudaGraphDestroy(gr);
     if (e != cudaSuccess) return fail(IJ_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
   }
+  if (h->cfg.lr_cosine && steps > 0)
+    CUDA_TRY(launch_schedule_begin(h->d_step, h->d_sched, steps, h->stream));
   for (int i = 0; i < steps; i++) CUDA_TRY(cudaGraphLaunch(h->gexec, h->stream));
   ij_status st = status_check(h);
   if (st != IJ_OK) return st;

@@ -40,7 +40,7 @@ class sg_config(C.Structure):
     _fields_ = [("members", C.c_int), ("hidden", C.c_int), ("batch", C.c_int),
                 ("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
                 ("seed", C.c_ulonglong), ("log_inputs", C.c_int), ("log_outputs", C.c_int),
-                ("out_weight", C.c_float * 4)]
+                ("out_weight", C.c_float * 4), ("lr_cosine", C.c_int)]
 
 
 _lib = ij._lib
@@ -85,7 +85,7 @@ def gemm_bf16(A, B, M, N, K, C_out, lda, ldb, ldc, stream=None):
 
 DEFAULT_CONFIG = dict(members=5, hidden=256, batch=256, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
                       seed=1, log_inputs=0b0011110, log_outputs=0b0101,
-                      out_weight=(1.0, 1.0, 1.0, 0.25))
+                      out_weight=(1.0, 1.0, 1.0, 0.25), lr_cosine=1)
 
 
 class Surrogate:
@@ -96,7 +96,7 @@ class Surrogate:
         c = dict(DEFAULT_CONFIG, **cfg)
         conf = sg_config(c["members"], c["hidden"], c["batch"], c["lr"], c["beta1"], c["beta2"],
                          c["eps"], c["seed"], c["log_inputs"], c["log_outputs"],
-                         (C.c_float * 4)(*c["out_weight"]))
+                         (C.c_float * 4)(*c["out_weight"]), int(c["lr_cosine"]))
         self.config = c
         s = torch.cuda.current_stream() if stream is None else stream
         raw = s.cuda_stream

@@ -80,11 +80,11 @@ def test_library_exports_every_surrogate_symbol():
 def test_surrogate_config_is_checked_on_the_host():
     from paper_1702_04487_gb300 import surrogate as S
     for bad in (dict(members=0), dict(members=9), dict(hidden=20), dict(hidden=512),
-                dict(batch=8), dict(lr=0.0), dict(beta1=1.0)):
+                dict(batch=8), dict(lr=0.0), dict(beta1=1.0), dict(lr_cosine=2)):
         c = dict(S.DEFAULT_CONFIG, **bad)
         conf = S.sg_config(c["members"], c["hidden"], c["batch"], c["lr"], c["beta1"], c["beta2"],
                            c["eps"], c["seed"], c["log_inputs"], c["log_outputs"],
-                           (C.c_float * 4)(*c["out_weight"]))
+                           (C.c_float * 4)(*c["out_weight"]), c["lr_cosine"])
         out = C.c_void_p(7)
         st = S._lib.sg_create(C.byref(conf), inkjet.ALLOC_FN(), inkjet.FREE_FN(), None, None,
                               C.byref(out))
